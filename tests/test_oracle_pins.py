@@ -1,0 +1,474 @@
+"""Pins of the FP64 oracle against facts other than itself: closed forms,
+library routines, Monte-Carlo and brute force.  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+from scipy.special import sph_harm_y
+
+import oracle
+from oracle import frag2mat as f2m
+from paper_2505_24796_gb300 import scenes
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def scene_arrays(sc):
+    return {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+
+
+def make_scene(means3, scales, quats, opacity, rgb):
+    """Degree-0 scene whose colours are exactly ``rgb`` (DC coefficient (rgb - 0.5) / Y00)."""
+    means3 = np.atleast_2d(np.asarray(means3, np.float64))
+    P = means3.shape[0]
+    y00 = 0.5 / math.sqrt(math.pi)
+    sh = ((np.asarray(rgb, np.float64).reshape(P, 3) - 0.5) / y00).reshape(P, 1, 3)
+    return dict(means3=means3, scales=np.asarray(scales, np.float64).reshape(P, 3),
+                quats=np.asarray(quats, np.float64).reshape(P, 4), opacity=np.asarray(opacity, np.float64).reshape(P),
+                sh=sh, sh_degree=0)
+
+
+# ---------------------------------------------------------------- projection
+
+def test_quaternion_matches_scipy():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        q = rng.standard_normal(4) * rng.uniform(0.1, 5.0)  # unnormalised on purpose
+        R = oracle.quat_to_rot(q)
+        ref = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy is (x, y, z, w)
+        np.testing.assert_allclose(R, ref, atol=1e-13)
+
+
+def _real_sh_3dgs(l, m, d):
+    """Real SH from scipy's complex SH (Condon-Shortley phase included), in the
+    sign convention of the 3DGS colour model: (-1)^m times the usual real form."""
+    x, y, z = d
+    theta = math.acos(max(-1.0, min(1.0, z)))
+    phi = math.atan2(y, x)
+    if m == 0:
+        val = sph_harm_y(l, 0, theta, phi).real
+    elif m > 0:
+        val = math.sqrt(2.0) * (-1) ** m * sph_harm_y(l, m, theta, phi).real
+    else:
+        val = math.sqrt(2.0) * (-1) ** m * sph_harm_y(l, -m, theta, phi).imag
+    return (-1) ** abs(m) * val
+
+
+def test_sh_basis_matches_scipy():
+    rng = np.random.default_rng(1)
+    for _ in range(40):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        got = oracle.sh_basis(3, d)
+        ref = [_real_sh_3dgs(l, m, d) for l in range(4) for m in range(-l, l + 1)]
+        np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+def test_sh_basis_orthonormal():
+    # Gauss-Legendre in cos(theta) x uniform phi: exact for these polynomial degrees
+    ct, w = np.polynomial.legendre.leggauss(24)
+    phis = np.linspace(0, 2 * np.pi, 48, endpoint=False)
+    G = np.zeros((16, 16))
+    for c, wc in zip(ct, w):
+        s = math.sqrt(1 - c * c)
+        for ph in phis:
+            Y = oracle.sh_basis(3, [s * math.cos(ph), s * math.sin(ph), c])
+            G += wc * (2 * np.pi / len(phis)) * np.outer(Y, Y)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_isotropic_on_axis_closed_form():
+    f, z, s = 300.0, 5.0, 0.04
+    cam = scenes.pinhole(320, 240, fx=f)
+    sc = make_scene([0, 0, z], [s, s, s], [0.3, -0.2, 0.5, 0.7], [0.5], [[0.2, 0.4, 0.6]])
+    pr = oracle.project(cam, sc)
+    var = (f * s / z) ** 2 + 0.3
+    np.testing.assert_allclose(pr["mean2d"][0], [160.0, 120.0], atol=1e-12)
+    np.testing.assert_allclose(pr["cov2d"][0], [var, 0.0, var], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(pr["conic"][0], [1 / var, 0.0, 1 / var], rtol=1e-12, atol=1e-15)
+    # isotropic: the eigen-gap term is floored at 0.1 (radius reading)
+    assert pr["radius"][0] == math.ceil(3 * math.sqrt(var + math.sqrt(0.1)))
+    assert pr["depth"][0] == z
+    np.testing.assert_allclose(pr["rgb"][0], [0.2, 0.4, 0.6], atol=1e-12)
+
+
+def _random_view(rng):
+    R = Rotation.from_rotvec(rng.normal(0, 0.3, 3)).as_matrix()
+    t = rng.normal(0, 0.5, 3)
+    return np.hstack([R, t[:, None]])
+
+
+def test_projection_matches_monte_carlo():
+    """EWA (Eq. 2) is the linearisation of the pinhole map: for a small Gaussian the
+    covariance of projected samples must match Sigma' - 0.3 I."""
+    rng = np.random.default_rng(2)
+    vm = _random_view(rng)
+    cam = scenes.pinhole(640, 480, fx=500.0, fy=450.0, viewmat=vm)
+    cam["viewmat"] = vm
+    R3, t3 = vm[:, :3], vm[:, 3]
+    target_cam = np.array([0.3, -0.2, 6.0])
+    mu = np.linalg.solve(R3, target_cam - t3)
+    scales = np.array([0.03, 0.012, 0.02])
+    q = np.array([0.8, 0.3, -0.4, 0.2])
+    sc = make_scene(mu, scales, q, [0.9], [[0.5, 0.5, 0.5]])
+    pr = oracle.project(cam, sc)
+    Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    n = 400_000
+    pts = mu[None, :] + (rng.standard_normal((n, 3)) * scales[None, :]) @ Rg.T
+    pc = pts @ R3.T + t3[None, :]
+    u = cam["fx"] * pc[:, 0] / pc[:, 2] + cam["cx"]
+    v = cam["fy"] * pc[:, 1] / pc[:, 2] + cam["cy"]
+    emp = np.cov(np.stack([u, v]))
+    a, b, c = pr["cov2d"][0]
+    ewa = np.array([[a - 0.3, b], [b, c - 0.3]])
+    np.testing.assert_allclose(emp, ewa, rtol=0.02, atol=0.02 * np.abs(ewa).max())
+    np.testing.assert_allclose(pr["mean2d"][0], [u.mean(), v.mean()], atol=0.02)
+
+
+def test_projection_numeric_jacobian():
+    """Sigma' equals J_num Sigma_world J_num^T + 0.3 I with J_num the finite-difference
+    Jacobian of the pinhole map of world points (no frustum clamp active)."""
+    rng = np.random.default_rng(3)
+    vm = _random_view(rng)
+    cam = scenes.pinhole(800, 600, fx=700.0, fy=650.0, viewmat=vm)
+    cam["viewmat"] = vm
+    R3, t3 = vm[:, :3], vm[:, 3]
+    for _ in range(20):
+        mu = np.linalg.solve(R3, np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(3, 8)]) - t3)
+        scales = np.exp(rng.normal(-3, 0.5, 3))
+        q = rng.standard_normal(4)
+        sc = make_scene(mu, scales, q, [0.5], [[0.5, 0.5, 0.5]])
+        pr = oracle.project(cam, sc)
+
+        def proj(p):
+            pc = R3 @ p + t3
+            return np.array([cam["fx"] * pc[0] / pc[2] + cam["cx"], cam["fy"] * pc[1] / pc[2] + cam["cy"]])
+
+        h = 1e-6
+        J = np.stack([(proj(mu + h * e) - proj(mu - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        Sw = Rg @ np.diag(scales ** 2) @ Rg.T
+        ref = J @ Sw @ J.T + 0.3 * np.eye(2)
+        a, b, c = pr["cov2d"][0]
+        np.testing.assert_allclose([a, b, c], [ref[0, 0], ref[0, 1], ref[1, 1]], rtol=1e-6, atol=1e-9)
+        lam = np.linalg.eigvalsh(ref)
+        mid, det = 0.5 * (a + c), a * c - b * b
+        lam1 = mid + math.sqrt(max(0.1, mid * mid - det))
+        assert lam1 >= lam.max() * (1 - 1e-6)
+
+
+def test_projection_culls_behind_near_plane():
+    cam = scenes.pinhole(64, 64, fx=64.0)
+    sc = make_scene([[0, 0, 0.1], [0, 0, -3], [0, 0, 2]], np.full((3, 3), 0.05), np.tile([1, 0, 0, 0], (3, 1)),
+                    [0.5, 0.5, 0.5], np.full((3, 3), 0.5))
+    pr = oracle.project(cam, sc)
+    assert list(pr["radius"][:2]) == [0, 0] and pr["radius"][2] > 0
+    assert list(pr["tiles_touched"][:2]) == [0, 0]
+
+
+def test_sh_colour_clamped_at_zero():
+    cam = scenes.pinhole(64, 64, fx=64.0)
+    sc = make_scene([0, 0, 3], [0.05] * 3, [1, 0, 0, 0], [0.5], [[-0.3, 0.2, 1.4]])
+    pr = oracle.project(cam, sc)
+    np.testing.assert_allclose(pr["rgb"][0], [0.0, 0.2, 1.4], atol=1e-12)
+
+
+def test_degree3_colour_uses_view_direction():
+    rng = np.random.default_rng(4)
+    cam = scenes.pinhole(256, 256, fx=200.0, campos=[0.1, -0.2, -0.5])
+    cam["campos"] = np.array([0.1, -0.2, -0.5])
+    mu = np.array([0.2, 0.1, 4.0])
+    sh = rng.normal(0, 0.3, (1, 16, 3))
+    sc = dict(means3=mu[None], scales=np.full((1, 3), 0.05), quats=np.array([[1.0, 0, 0, 0]]),
+              opacity=np.array([0.5]), sh=sh, sh_degree=3)
+    pr = oracle.project(cam, sc)
+    d = mu - cam["campos"]
+    d /= np.linalg.norm(d)
+    Y = np.array([_real_sh_3dgs(l, m, d) for l in range(4) for m in range(-l, l + 1)])
+    np.testing.assert_allclose(pr["rgb"][0], np.maximum(Y @ sh[0] + 0.5, 0.0), atol=1e-12)
+
+
+# ---------------------------------------------------------------- binning
+
+def _brute_splats(cam, mean2d, radius, depth):
+    gw, gh = oracle.grid(cam)
+    out = []
+    for g in range(len(radius)):
+        r = radius[g]
+        if r <= 0:
+            continue
+        for ty in range(gh):
+            for tx in range(gw):
+                inx = mean2d[g, 0] - r < 16 * tx + 16 and mean2d[g, 0] + r >= 16 * tx
+                iny = mean2d[g, 1] - r < 16 * ty + 16 and mean2d[g, 1] + r >= 16 * ty
+                if inx and iny:
+                    out.append((ty * gw + tx, depth[g], g))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_binning_matches_brute_force(seed):
+    cam, sc = scenes.plain_forward(P=150, width=72, height=56, seed=seed)
+    pr = oracle.project(cam, sc)
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    ref = _brute_splats(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    assert b["n"] == len(ref) == int(pr["tiles_touched"].sum())
+    assert list(b["tile_of"]) == [t for t, _, _ in ref]
+    assert list(b["ids"]) == [g for _, _, g in ref]
+    gw, gh = oracle.grid(cam)
+    for t in range(gw * gh):
+        members = [i for i, (tt, _, _) in enumerate(ref) if tt == t]
+        if members:
+            assert tuple(b["ranges"][t]) == (members[0], members[-1] + 1)
+        else:
+            assert b["ranges"][t, 0] == b["ranges"][t, 1]
+
+
+def test_binning_depth_ties_ordered_by_index():
+    cam = scenes.pinhole(32, 32, fx=32.0)
+    mean2d = np.array([[10.0, 10.0], [12.0, 9.0], [11.0, 11.0]])
+    radius = np.array([3, 3, 3], np.int32)
+    depth = np.array([2.0, 1.0, 2.0])
+    b = oracle.bin_sort(cam, mean2d, radius, depth)
+    assert list(b["ids"]) == [1, 0, 2]
+
+
+# ---------------------------------------------------------------- rendering
+
+def _render_scene(cam, sc, alpha_max=0.99, bg=(0, 0, 0)):
+    pr = oracle.project(cam, sc)
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    op = np.asarray(sc["opacity"], np.float64)
+    out = oracle.render(cam, b, pr["mean2d"], pr["conic"], op, pr["rgb"], bg=bg, alpha_max=alpha_max)
+    return pr, b, out
+
+
+def test_single_gaussian_closed_form():
+    cam = scenes.pinhole(48, 40, fx=60.0)
+    sc = make_scene([0.05, -0.03, 3.0], [0.08, 0.05, 0.06], [0.9, 0.1, 0.3, -0.2], [0.8], [[0.9, 0.3, 0.1]])
+    pr, b, out = _render_scene(cam, sc)
+    a_, b_, c_ = pr["cov2d"][0]
+    Q = np.linalg.inv(np.array([[a_, b_], [b_, c_]]))  # conic from the covariance, independently
+    m, (s11, s12, s22) = pr["mean2d"][0], (Q[0, 0], Q[0, 1], Q[1, 1])
+    j, i = np.meshgrid(np.arange(40) + 0.5, np.arange(48) + 0.5, indexing="ij")
+    dx, dy = m[0] - i, m[1] - j
+    a = np.minimum(0.99, 0.8 * np.exp(-0.5 * (s11 * dx * dx + 2 * s12 * dx * dy + s22 * dy * dy)))
+    # only pixels of covered tiles see the Gaussian
+    gw, _ = oracle.grid(cam)
+    tile = (j.astype(int) // 16) * gw + (i.astype(int) // 16)
+    covered = np.isin(tile, b["tile_of"])
+    a = np.where((a >= 1 / 255) & covered, a, 0.0)
+    for ch, c in enumerate([0.9, 0.3, 0.1]):
+        np.testing.assert_allclose(out["img"][ch], c * a, atol=1e-12)
+    np.testing.assert_allclose(out["T"], 1 - a, atol=1e-12)
+
+
+def test_two_colocated_gaussians_closed_form():
+    cam = scenes.pinhole(32, 32, fx=40.0)
+    sc = make_scene([[0, 0, 2.0], [0, 0, 3.0]], [[0.1] * 3, [0.15] * 3], [[1, 0, 0, 0]] * 2, [0.6, 0.7],
+                    [[1, 0, 0], [0, 1, 0]])
+    pr, b, out = _render_scene(cam, sc)
+    p = (16, 16)  # pixel centre (16.5, 16.5); mean at (16, 16)
+    a = []
+    for g in range(2):
+        d = pr["mean2d"][g] - np.array([16.5, 16.5])
+        s11, s12, s22 = pr["conic"][g]
+        a.append(min(0.99, sc["opacity"][g] * math.exp(-0.5 * (s11 * d[0] ** 2 + 2 * s12 * d[0] * d[1] + s22 * d[1] ** 2))))
+    assert abs(out["img"][0][p] - a[0]) < 1e-13
+    assert abs(out["img"][1][p] - a[1] * (1 - a[0])) < 1e-13
+    assert abs(out["T"][p] - (1 - a[0]) * (1 - a[1])) < 1e-13
+
+
+def test_termination_index():
+    """Five co-located Gaussians with alpha 0.95 at the centre: T runs 1, .05, .0025,
+    1.25e-4; the fourth would give 6.25e-6 < 1e-4, so it breaks there unblended."""
+    cam = scenes.pinhole(17, 17, fx=17.0)  # cx = 8.5: pixel (8, 8) samples the mean exactly
+    P = 5
+    sc = make_scene(np.tile([0.0, 0.0, 0.0], (P, 1)) + np.array([[0, 0, 2.0 + 0.1 * k] for k in range(P)]),
+                    np.full((P, 3), 1.0), np.tile([1, 0, 0, 0], (P, 1)), np.full(P, 0.95), np.full((P, 3), 1.0))
+    pr, b, out = _render_scene(cam, sc, alpha_max=1.0)
+    p = (8, 8)
+    d = pr["mean2d"][0] - np.array([8.5, 8.5])
+    assert np.abs(d).max() < 1e-12
+    assert out["n_contrib"][p] == 3 and out["n_eval"][p] == 4
+    assert abs(out["T"][p] - 0.05 ** 3) < 1e-15
+
+
+def test_alg1_literal_opaque_gaussian_breaks_unblended():
+    """With alpha_max = 1 (no clamp) an alpha = 1 fragment fails T - aT >= 1e-4 at once
+    and Algorithm 1 breaks without blending it; the 0.99 clamp keeps it."""
+    cam = scenes.pinhole(17, 17, fx=17.0)
+    sc = make_scene([0, 0, 2.0], [1.0, 1.0, 1.0], [1, 0, 0, 0], [1.0], [[1, 1, 1]])
+    _, _, lit = _render_scene(cam, sc, alpha_max=1.0)
+    _, _, clamped = _render_scene(cam, sc, alpha_max=0.99)
+    assert lit["img"][0, 8, 8] == 0.0 and lit["T"][8, 8] == 1.0
+    assert abs(clamped["img"][0, 8, 8] - 0.99) < 1e-15
+
+
+def test_cull_threshold():
+    cam = scenes.pinhole(17, 17, fx=17.0)
+    for o, seen in [(1 / 255 * 0.999, False), (1 / 255 * 1.001, True)]:
+        sc = make_scene([0, 0, 2.0], [1.0, 1.0, 1.0], [1, 0, 0, 0], [o], [[1, 1, 1]])
+        _, _, out = _render_scene(cam, sc)
+        assert (out["img"][0, 8, 8] > 0) == seen
+
+
+def test_white_composite_equals_one_minus_T_and_T_monotone():
+    cam, sc = scenes.plain_forward(P=300, width=64, height=48, seed=7)
+    sc["sh"][:] = 0.5 / (0.5 / math.sqrt(math.pi))  # colour exactly 1
+    pr, b, out = _render_scene(cam, scene_arrays(sc))
+    np.testing.assert_allclose(out["img"][0], 1 - out["T"], atol=1e-12)
+    assert (out["T"] > 0).all() and (out["T"] <= 1).all()
+    # T along each pixel's list never increases: check with growing list prefixes
+    b2 = dict(b)
+    prev = np.ones_like(out["T"])
+    for cut in [1, 2, 4, 8, 16, 10 ** 9]:
+        r = b["ranges"].copy()
+        r[:, 1] = np.minimum(r[:, 1], r[:, 0] + cut)
+        b2["ranges"] = r
+        o2 = oracle.render(cam, b2, pr["mean2d"], pr["conic"], sc["opacity"], pr["rgb"])
+        assert (o2["T"] <= prev + 1e-15).all()
+        prev = o2["T"]
+
+
+@pytest.mark.parametrize("seed,bg", [(0, (0, 0, 0)), (1, (0.2, 0.5, 0.9))])
+def test_tiled_equals_untiled_bruteforce(seed, bg):
+    cam, sc = scenes.plain_forward(P=200, width=56, height=40, seed=seed)
+    sc = scene_arrays(sc)
+    pr, b, out = _render_scene(cam, sc, bg=bg)
+    bf = oracle.render_bruteforce(cam, pr["mean2d"], pr["radius"], pr["depth"], pr["conic"], sc["opacity"],
+                                  pr["rgb"], bg=bg)
+    assert np.array_equal(out["img"], bf["img"])
+    assert np.array_equal(out["T"], bf["T"])
+    assert np.array_equal(out["n_contrib"], bf["n_contrib"])
+
+
+def test_fragment_counts_consistent():
+    cam, sc = scenes.plain_forward(P=300, width=64, height=64, seed=5)
+    pr, b, out = _render_scene(cam, scene_arrays(sc))
+    assert out["f_blend"] + out["f_cull"] == out["alpha_evals"] == int(out["n_eval"].sum())
+    assert (out["n_contrib"] <= out["n_eval"]).all()
+
+
+# ---------------------------------------------------------------- Frag2Mat / G2L
+
+def test_frag2mat_identity_global_and_local():
+    rng = np.random.default_rng(8)
+    n = 64
+    mean2d = rng.uniform(0, 200, (n, 2))
+    L = rng.normal(0, 0.5, (n, 2, 2))
+    Q = np.einsum("nij,nkj->nik", L, L) + 0.05 * np.eye(2)
+    conic = np.stack([Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 1]], 1)
+    o = rng.uniform(0.01, 1, n)
+    px, py = rng.uniform(0, 200, 100), rng.uniform(0, 200, 100)
+    ref = f2m.beta_direct(px, py, mean2d, conic, o)
+    got = f2m.pixel_vectors(px, py) @ f2m.gaussian_vectors(mean2d, conic, o).T
+    np.testing.assert_allclose(got, ref, atol=1e-9 * np.abs(ref).max())
+    # G2L: shifting pixels and means by the same tile centre leaves beta unchanged
+    c = f2m.tile_centre(3, 5)
+    got_l = f2m.pixel_vectors(px - c[0], py - c[1]) @ f2m.gaussian_vectors(mean2d - c, conic, o).T
+    np.testing.assert_allclose(got_l, ref, atol=1e-9 * np.abs(ref).max())
+
+
+def test_g2l_pixel_vectors_small_and_exact_in_fp16():
+    dx, dy = f2m.tile_pixels_local()
+    U = f2m.pixel_vectors(dx, dy)
+    assert np.abs(U).max() <= GOLD["local_max_u"]["value"]
+    assert np.abs(np.stack([dx, dy])).max() <= GOLD["local_range"]["value"]
+    assert np.array_equal(f2m.round_f16(U), U)
+
+
+def _emulate_tc(U, V, dtype=np.float16):
+    """Tensor-core dot products: inputs rounded to ``dtype``, exact products, FP32
+    accumulation left to right (Appendix A's model)."""
+    Ur = U.astype(dtype).astype(np.float64)
+    Vr = V.astype(dtype).astype(np.float64)
+    acc = np.zeros((U.shape[0], V.shape[0]), np.float32)
+    for k in range(U.shape[1]):
+        acc = (acc.astype(np.float64) + np.outer(Ur[:, k], Vr[:, k])).astype(np.float32)
+    return acc.astype(np.float64)
+
+
+def test_appendix_bound_holds_for_emulated_fp16_local():
+    cam, sc = scenes.plain_forward(P=400, width=96, height=96, seed=9)
+    pr = oracle.project(cam, scene_arrays(sc))
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    gw, gh = oracle.grid(cam)
+    checked = 0
+    for t in range(gw * gh):
+        s, e = b["ranges"][t]
+        ids = b["ids"][s:e]
+        if len(ids) == 0:
+            continue
+        U, V, beta, absum = f2m.local_products(t % gw, t // gw, pr["mean2d"][ids], pr["conic"][ids],
+                                               sc["opacity"][ids])
+        bh = _emulate_tc(U, V)
+        keep = beta >= -math.log(255.0)  # the bound is stated for fragments that are not culled
+        err = np.abs(bh - beta)
+        assert (err[keep] <= f2m.paper_bound(absum)[keep] + 1e-5).all()
+        checked += keep.sum()
+    assert checked > 1000
+
+
+def test_global_fp16_overflows_at_1920px():
+    """Sec. 4.3: global pixel coordinates make u's quadratic terms overflow FP16."""
+    U = f2m.pixel_vectors(np.array([1919.5]), np.array([1079.5]))
+    assert np.isinf(U.astype(np.float16)).any()
+
+
+def test_constants_match_paper():
+    assert abs(f2m.EPS_H - GOLD["eps_H"]["value"]) < 5e-7
+    assert abs(f2m.EPS_F - GOLD["eps_F"]["value"]) < 5e-10
+    assert abs(-math.log(255.0) - GOLD["early_cull_beta"]["value"]) < 1e-12
+    assert abs(1 / 255 - GOLD["cull_alpha"]["value"]) < 1e-15
+
+
+# ---------------------------------------------------------------- backward
+
+def _fd_setup(seed=11):
+    cam, sc = scenes.plain_forward(P=200, width=64, height=64, seed=seed)
+    pr = oracle.project(cam, scene_arrays(sc))
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    rng = np.random.default_rng(seed)
+    gimg = rng.standard_normal((3, 64, 64))
+    return cam, sc, pr, b, gimg
+
+
+def test_backward_matches_finite_differences():
+    cam, sc, pr, b, gimg = _fd_setup()
+    op = np.asarray(sc["opacity"], np.float64)
+    base = dict(mean2d=pr["mean2d"].copy(), conic=pr["conic"].copy(), opacity=op.copy(), rgb=pr["rgb"].copy())
+    g = oracle.render_bwd(cam, b, base["mean2d"], base["conic"], base["opacity"], base["rgb"], gimg)
+    grads = dict(mean2d=g["dmean2d"], conic=g["dconic"], opacity=g["dopacity"], rgb=g["drgb"])
+    ref = oracle.render(cam, b, **base)
+
+    def loss(p):
+        o = oracle.render(cam, b, p["mean2d"], p["conic"], p["opacity"], p["rgb"])
+        stable = (np.array_equal(o["n_contrib"], ref["n_contrib"]) and np.array_equal(o["n_eval"], ref["n_eval"]))
+        return float((o["img"] * gimg).sum()), stable
+
+    rng = np.random.default_rng(0)
+    visible = np.nonzero(pr["radius"] > 0)[0]
+    # pick Gaussians with non-negligible gradient
+    mag = np.abs(g["dopacity"][visible])
+    cand = visible[np.argsort(-mag)[:40]]
+    n_checked = 0
+    for name, h in [("mean2d", 1e-5), ("conic", 1e-7), ("opacity", 1e-7), ("rgb", 1e-6)]:
+        for gid in rng.choice(cand, 6, replace=False):
+            for k in range(base[name].reshape(len(op), -1).shape[1]):
+                p_plus = {kk: vv.copy() for kk, vv in base.items()}
+                p_minus = {kk: vv.copy() for kk, vv in base.items()}
+                p_plus[name].reshape(len(op), -1)[gid, k] += h
+                p_minus[name].reshape(len(op), -1)[gid, k] -= h
+                lp, s1 = loss(p_plus)
+                lm, s2 = loss(p_minus)
+                if not (s1 and s2):
+                    continue  # a cull / termination decision flipped: not differentiable here
+                fd = (lp - lm) / (2 * h)
+                an = grads[name].reshape(len(op), -1)[gid, k]
+                assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (name, gid, k, fd, an)
+                n_checked += 1
+    assert n_checked > 40
