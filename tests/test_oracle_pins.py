@@ -472,3 +472,39 @@ def test_backward_matches_finite_differences():
                 assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (name, gid, k, fd, an)
                 n_checked += 1
     assert n_checked > 40
+
+
+def test_backward_clamped_alpha_finite_differences():
+    """Fragments whose alpha hits the 0.99 clamp carry no gradient through the
+    exponent; a near-opaque Gaussian over several pixels exercises that branch."""
+    cam = scenes.pinhole(32, 32, fx=32.0)
+    sc = make_scene([[0.02, -0.01, 2.0], [0.1, 0.05, 3.0], [-0.2, 0.1, 2.5]],
+                    [[0.5, 0.45, 0.4], [0.2, 0.15, 0.1], [0.1, 0.3, 0.1]],
+                    [[1, 0, 0, 0], [0.9, 0.2, 0.1, 0.3], [0.7, -0.3, 0.2, 0.1]],
+                    [0.9995, 0.6, 0.8], [[0.9, 0.2, 0.3], [0.1, 0.8, 0.3], [0.4, 0.4, 0.9]])
+    pr = oracle.project(cam, sc)
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    base = dict(mean2d=pr["mean2d"].copy(), conic=pr["conic"].copy(), opacity=sc["opacity"].copy(),
+                rgb=pr["rgb"].copy())
+    ref = oracle.render(cam, b, **base)
+    d = ref["img"]  # sanity: the clamp is active at some pixel
+    q = base["conic"][0]
+    j, i = np.meshgrid(np.arange(32) + 0.5, np.arange(32) + 0.5, indexing="ij")
+    dx, dy = base["mean2d"][0, 0] - i, base["mean2d"][0, 1] - j
+    raw = 0.9995 * np.exp(-0.5 * (q[0] * dx * dx + 2 * q[1] * dx * dy + q[2] * dy * dy))
+    assert (raw > 0.99).sum() >= 2 and d.max() > 0
+    gimg = np.random.default_rng(5).standard_normal((3, 32, 32))
+    g = oracle.render_bwd(cam, b, base["mean2d"], base["conic"], base["opacity"], base["rgb"], gimg)
+    grads = dict(mean2d=g["dmean2d"], conic=g["dconic"], opacity=g["dopacity"], rgb=g["drgb"])
+    for name, h in [("mean2d", 1e-6), ("conic", 1e-8), ("opacity", 1e-8)]:
+        arr = base[name].reshape(3, -1)
+        for k in range(arr.shape[1]):
+            pp = {kk: vv.copy() for kk, vv in base.items()}
+            pm = {kk: vv.copy() for kk, vv in base.items()}
+            pp[name].reshape(3, -1)[0, k] += h
+            pm[name].reshape(3, -1)[0, k] -= h
+            op_, om_ = oracle.render(cam, b, **pp), oracle.render(cam, b, **pm)
+            assert np.array_equal(op_["n_contrib"], ref["n_contrib"])
+            fd = ((op_["img"] * gimg).sum() - (om_["img"] * gimg).sum()) / (2 * h)
+            an = grads[name].reshape(3, -1)[0, k]
+            assert abs(fd - an) <= 2e-5 * max(1.0, abs(an)), (name, k, fd, an)
