@@ -1,0 +1,195 @@
+/*
+ * tcgs.h -- C ABI of the GB300 (sm_103a) TC-GS rasterizer library (libtcgs.so).
+ *
+ * TC-GS ("A Faster Gaussian Splatting Module Utilizing Tensor Cores") renders
+ * 3D Gaussian Splatting scenes in three stages (Sec. 3.1): preprocess
+ * (projection), sorting (tile binning + depth sort) and conditional
+ * alpha-blending (Algorithm 1).  Its contribution is the third stage:
+ * EarlyCull (Sec. 4.1), Frag2Mat (Sec. 4.2, the exponent of every
+ * pixel-Gaussian pair as one matrix product B = U^T V on tensor cores) and
+ * G2L (Sec. 4.3, tile-local coordinates so the quadratic pixel terms survive
+ * half precision).
+ *
+ * General rules for every call:
+ *   - All array arguments are DEVICE pointers owned by the caller, unless the
+ *     argument's comment says "host".  The library never allocates, frees or
+ *     keeps a pointer after the call returns.
+ *   - Every call only enqueues work on `stream` (NULL = the legacy default
+ *     stream) and returns without synchronising.  Argument errors are detected
+ *     on the host and returned at once (TCGS_ERR_INVALID, nothing enqueued).
+ *     A launch failure returns TCGS_ERR_CUDA.  Errors found on the device
+ *     (capacity overflow, a timed-out wait) are written to a caller-provided
+ *     device status word, readable after the stream is synchronised.
+ *   - Arrays are dense, row-major, float32 unless stated otherwise.
+ *   - Pixel (i, j) is sampled at (i + 0.5, j + 0.5).  Tiles are 16 x 16
+ *     pixels, numbered row-major: tile = ty * ceil(W / 16) + tx.
+ *   - Gradient outputs are ACCUMULATED (+=): the caller zeroes them.
+ */
+#ifndef TCGS_H
+#define TCGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TCGS_API __attribute__((visibility("default")))
+#else
+#define TCGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (CUstream); NULL selects the legacy default stream. */
+typedef struct CUstream_st* tcgs_stream;
+
+typedef enum {
+    TCGS_OK = 0,
+    TCGS_ERR_INVALID = 1,     /* bad argument (null pointer, negative size, unsupported option) */
+    TCGS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    TCGS_ERR_CAPACITY = 3,    /* more splats than the caller's capacity (device status word) */
+    TCGS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (device status word) */
+    TCGS_ERR_UNSUPPORTED = 5  /* the current device cannot run this call (not sm_103a) */
+} tcgs_status;
+
+/* How the exponent beta = ln(o) - 1/2 d^T Sigma'^-1 d of Eq. (9) is evaluated. */
+typedef enum {
+    TCGS_FP32 = 0,          /* CUDA cores, FP32, Eq. (4) per fragment: the 3DGS baseline */
+    TCGS_TC_FP16 = 1,       /* Frag2Mat + G2L on tensor cores, FP16 inputs, FP32 accumulate, with
+                               the paper's K = 8 padding (v0 / 3 in three slots, Sec. 5.1) */
+    TCGS_TC_FP16_SPLIT = 2, /* as TC_FP16 but v = v_hi + v_lo in FP16 over K = 16 (u duplicated) */
+    TCGS_TC_FP8 = 3         /* trial: U and V in FP8 e4m3, FP32 accumulate (accuracy reported only) */
+} tcgs_precision;
+
+/* Pinhole camera.  mean2d = (fx X / Z + cx, fy Y / Z + cy) for camera-space (X, Y, Z). */
+typedef struct {
+    int32_t width, height;     /* image size in pixels (>= 1) */
+    float fx, fy, cx, cy;      /* focal lengths and principal point, pixels */
+    float viewmat[12];         /* row-major 3x4 world -> camera [R | t] */
+    float campos[3];           /* camera centre in world coordinates (SH view direction) */
+    float near_z;              /* Gaussians with camera Z <= near_z are culled */
+    float tan_fovx, tan_fovy;  /* frustum clamp of the Jacobian at 1.3 tan; <= 0: W / (2 fx), H / (2 fy) */
+} tcgs_camera;
+
+/* Options of the alpha-blending calls. */
+typedef struct {
+    int32_t precision;       /* tcgs_precision */
+    float alpha_max;         /* alpha clamp (0.99 as in the official 3DGS renderer; 1 = Algorithm 1 literally) */
+    int32_t early_cull;      /* FP32 path only: test beta < -ln 255 before exp (Sec. 4.1); TC paths always do */
+    uint32_t* tile_stats;    /* nullable device [num_tiles * 4], accumulated (+=) per tile:
+                                [0] blended fragments, [1] evaluated but not blended fragments
+                                (culled, plus the fragment that triggers termination),
+                                [2] fragment slots the kernel executed (pixels x list entries walked),
+                                [3] list length n(T) (added once per launch) */
+    int32_t* device_status;  /* nullable device int32: set to a tcgs_status on a device-side error */
+} tcgs_render_opts;
+
+/* Human-readable name of a status code (static string). */
+TCGS_API const char* tcgs_status_string(int status);
+
+/* Library version, 100 * major + minor. */
+TCGS_API int tcgs_version(void);
+
+/*
+ * Preprocess (Sec. 3.1, Eq. 2): EWA projection of P 3D Gaussians.
+ *   Sigma = R(q) diag(s)^2 R(q)^T, t = W mu, J = d(mean2d)/d(t) at t with x/z, y/z
+ *   clamped to +-1.3 tan_fov, Sigma' = J W Sigma W^T J^T + 0.3 I (low-pass dilation),
+ *   conic = Sigma'^-1 = (sigma11, sigma12, sigma22), radius = ceil(3 sqrt(lambda_max)),
+ *   lambda_max = m + sqrt(max(0.1, m^2 - det)), m = (a + c) / 2.
+ *   Colour = sum_k sh[k] Y_k(dir) + 0.5 clamped at 0, dir = (mu - campos) / |mu - campos|,
+ *   real SH up to degree 3 (3DGS convention).
+ * In:  means3 [P,3]; scales [P,3] (standard deviations, > 0); quats [P,4] (w,x,y,z, any
+ *      non-zero norm); sh [P, (sh_degree+1)^2, 3]; 0 <= sh_degree <= 3.
+ * Out: mean2d [P,2]; conic [P,3]; depth [P] (camera Z); radius [P] int32 (0 = culled: behind the
+ *      near plane, degenerate, or touching no tile); rgb [P,3]; tiles_touched [P] uint32.
+ *      Culled Gaussians get zeros in every output.
+ * P = 0 is valid (nothing is launched).
+ */
+TCGS_API tcgs_status tcgs_project(const tcgs_camera* cam /* host */, int32_t P, int32_t sh_degree,
+                         const float* means3, const float* scales, const float* quats, const float* sh,
+                         float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
+                         uint32_t* tiles_touched, tcgs_stream stream);
+
+/* Bytes of device workspace tcgs_bin_sort needs (a pure host function). */
+TCGS_API size_t tcgs_bin_sort_workspace_size(int32_t P, int64_t splat_capacity, int32_t num_tiles);
+
+/*
+ * Sorting stage (Sec. 3.1, Eq. 3): build the splats (tile, Gaussian), order every tile's
+ * list by increasing depth (ties: increasing Gaussian index) and find each tile's range.
+ * Gaussian g covers tile (tx, ty) iff [mx - r, mx + r] x [my - r, my + r] meets the tile's
+ * pixel square [16 tx, 16 tx + 16) x [16 ty, 16 ty + 16), r = radius[g] > 0.
+ * The order is the (tile, depth-bits) key order of the paper's radix sort; it is produced by
+ * an LSD radix sort whose depth digits run before duplication (on P keys) and whose tile
+ * digits run after it (on N keys).
+ * In:  mean2d [P,2], radius [P], depth [P] (> 0 where radius > 0).
+ * Out: ids_sorted [splat_capacity] uint32 (first N entries valid), tile_ranges [num_tiles, 2]
+ *      uint32 [start, end), n_splats: device int64 = N, status: device int32 (TCGS_OK, or
+ *      TCGS_ERR_CAPACITY when N > splat_capacity; then ids_sorted is untouched and every range
+ *      is empty).
+ * workspace: device, ws_bytes >= tcgs_bin_sort_workspace_size(P, splat_capacity, num_tiles),
+ *      256-byte aligned; contents are scratch.  splat_capacity <= 2^32 - 1.
+ */
+TCGS_API tcgs_status tcgs_bin_sort(const tcgs_camera* cam /* host */, int32_t P, const float* mean2d,
+                          const int32_t* radius, const float* depth, int64_t splat_capacity,
+                          void* workspace, size_t ws_bytes, uint32_t* ids_sorted, uint32_t* tile_ranges,
+                          int64_t* n_splats, int32_t* status, tcgs_stream stream);
+
+/*
+ * Conditional alpha-blending (Algorithm 1), front to back per pixel over its tile's list:
+ *   alpha = min(alpha_max, o exp(beta)), beta from Eq. (9);  cull if alpha < 1/255 (Eq. 5; the
+ *   TC paths test beta < -ln 255 first, Sec. 4.1);  break (without blending) if
+ *   T - alpha T < 1e-4;  C += c alpha T;  T -= alpha T.  Final colour C + T bg.
+ * TC precisions compute every beta of a 128-pixel half tile and a batch of Gaussians as one
+ * tcgen05 MMA (Eq. 18) in tile-local coordinates (Sec. 4.3) and need sm_103a.
+ * In:  tile_ranges, ids_sorted from tcgs_bin_sort; mean2d [P,2]; conic [P,3]; opacity [P] in
+ *      (0, 1]; rgb [P,3]; bg3: host float[3] background.
+ * Out: img [3,H,W]; T_final [H,W]; n_contrib [H,W] uint32 = 1 + (list index of the last blended
+ *      fragment), 0 if none.
+ * TC preconditions: the largest eigenvalue of the conic is at most 1000 px^-2 (the projection's
+ *      0.3 px^2 dilation keeps it below 3.34); otherwise FP16 saturates and the result is
+ *      unspecified (finite).
+ */
+TCGS_API tcgs_status tcgs_render_fwd(const tcgs_camera* cam /* host */, const tcgs_render_opts* opts /* host */,
+                            const uint32_t* tile_ranges, const uint32_t* ids_sorted, const float* mean2d,
+                            const float* conic, const float* opacity, const float* rgb,
+                            const float* bg3 /* host */, float* img, float* T_final, uint32_t* n_contrib,
+                            tcgs_stream stream);
+
+/*
+ * Backward of Algorithm 1 (C = sum_j c_j a_j T_j + bg T_final, Eq. 6) w.r.t. mean2d, conic,
+ * opacity and rgb, replaying each pixel's fragments 0 .. n_contrib-1 front to back with the
+ * FP32 forward's alpha arithmetic:
+ *   dL/dc_j = a_j T_j g;  dL/da_j = g . (c_j T_j - S_j / (1 - a_j)), S_j = colour blended after j
+ *   plus bg T_final;  through a = o exp(p) when unclamped: dL/do = dL/da a / o,
+ *   dL/dp = dL/da a, dp/dmean = -Q d, dp/dsigma11 = -d_x^2 / 2, dp/dsigma12 = -d_x d_y,
+ *   dp/dsigma22 = -d_y^2 / 2 (d = mean2d - pixel).  Clamped fragments pass no gradient to p, o.
+ * In:  as tcgs_render_fwd plus its outputs img, T_final, n_contrib, and dL_dimg [3,H,W].
+ * Out (accumulated): dmean2d [P,2], dconic [P,3], dopacity [P], drgb [P,3].
+ * opts->precision is ignored (the replay is FP32); opts->alpha_max must match the forward.
+ */
+TCGS_API tcgs_status tcgs_render_bwd(const tcgs_camera* cam /* host */, const tcgs_render_opts* opts /* host */,
+                            const uint32_t* tile_ranges, const uint32_t* ids_sorted, const float* mean2d,
+                            const float* conic, const float* opacity, const float* rgb,
+                            const float* bg3 /* host */, const float* img, const float* T_final,
+                            const uint32_t* n_contrib, const float* dL_dimg, float* dmean2d, float* dconic,
+                            float* dopacity, float* drgb, tcgs_stream stream);
+
+/*
+ * Frag2Mat exponents as the tensor cores compute them (Eq. 18, G2L frame of Sec. 4.3), for
+ * inspection against the error bound of Appendix A.  For each of n_tiles tiles (device
+ * tiles[n_tiles] int32) and each of the first min(max_n, n(T)) list entries, writes
+ * beta_hat in natural-log units to beta_out [n_tiles, 256, max_n] (pixel-major within the tile,
+ * row-major pixels; entries past the list end are set to -INFINITY).
+ * precision: TCGS_TC_FP16 or TCGS_TC_FP16_SPLIT (or TCGS_TC_FP8).
+ */
+TCGS_API tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam /* host */, int32_t precision, const uint32_t* tile_ranges,
+                               const uint32_t* ids_sorted, const float* mean2d, const float* conic,
+                               const float* opacity, int32_t n_tiles, const int32_t* tiles, int32_t max_n,
+                               float* beta_out, int32_t* device_status, tcgs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCGS_H */

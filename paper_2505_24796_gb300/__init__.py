@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) TC-GS rasterizer: PyTorch-facing binding of libtcgs.so.
+
+The functions named ``tcgs_*`` mirror the C ABI in ``include/tcgs.h`` one to
+one; they only check tensors, allocate outputs with PyTorch when the caller
+does not pass them, and hand raw device pointers and the current CUDA stream to
+the library.  Every step of the rasterizer runs in the library's CUDA kernels;
+nothing here computes on the CPU and there is no fallback path.
+
+``Renderer`` owns preallocated buffers for one camera and scene size and runs a
+whole frame (project -> bin_sort -> render_fwd) without host synchronisation.
+``rasterize`` is the differentiable alpha-blending stage (torch.autograd).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS_TC_FP8, TcgsError, check,
+                   tcgs_camera, tcgs_render_opts)
+
+TILE = 16
+
+__all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_render_fwd", "tcgs_render_bwd",
+           "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "TcgsError", "PRECISIONS",
+           "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8"]
+
+
+def _L():
+    return _lib.load()
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, name="tensor") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def make_camera(cam: dict) -> tcgs_camera:
+    """C camera struct from the plain-dict camera of ``scenes``."""
+    c = tcgs_camera()
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.fx, c.fy, c.cx, c.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    c.viewmat[:] = [float(v) for v in np.asarray(cam["viewmat"], dtype=np.float64).reshape(12)]
+    c.campos[:] = [float(v) for v in np.asarray(cam["campos"], dtype=np.float64).reshape(3)]
+    c.near_z = float(cam.get("near_z", 0.2))
+    c.tan_fovx = float(cam.get("tan_fovx", 0.0))
+    c.tan_fovy = float(cam.get("tan_fovy", 0.0))
+    return c
+
+
+def grid(cam) -> tuple[int, int]:
+    w, h = (cam.width, cam.height) if isinstance(cam, tcgs_camera) else (int(cam["width"]), int(cam["height"]))
+    return (w + TILE - 1) // TILE, (h + TILE - 1) // TILE
+
+
+def _cam(cam) -> tcgs_camera:
+    return cam if isinstance(cam, tcgs_camera) else make_camera(cam)
+
+
+def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=False, tile_stats=None,
+                device_status=None) -> tcgs_render_opts:
+    o = tcgs_render_opts()
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.alpha_max = float(alpha_max)
+    o.early_cull = int(bool(early_cull))
+    o.tile_stats = _ptr(tile_stats, torch.int32, "tile_stats") if tile_stats is not None else None
+    o.device_status = _ptr(device_status, torch.int32, "device_status") if device_status is not None else None
+    return o
+
+
+# ---------------------------------------------------------------- one-to-one C ABI wrappers
+
+def tcgs_project(cam, means3, scales, quats, sh, sh_degree, out=None, stream=None) -> dict:
+    c = _cam(cam)
+    P = means3.shape[0]
+    dev = means3.device
+    if out is None:
+        out = dict(mean2d=torch.empty(P, 2, device=dev), conic=torch.empty(P, 3, device=dev),
+                   depth=torch.empty(P, device=dev), radius=torch.empty(P, dtype=torch.int32, device=dev),
+                   rgb=torch.empty(P, 3, device=dev), tiles_touched=torch.empty(P, dtype=torch.int32, device=dev))
+    f = torch.float32
+    check("tcgs_project", _L().tcgs_project(
+        ctypes.byref(c), P, int(sh_degree), _ptr(means3, f, "means3"), _ptr(scales, f, "scales"),
+        _ptr(quats, f, "quats"), _ptr(sh, f, "sh"), _ptr(out["mean2d"], f), _ptr(out["conic"], f),
+        _ptr(out["depth"], f), _ptr(out["radius"], torch.int32), _ptr(out["rgb"], f),
+        _ptr(out["tiles_touched"], torch.int32), _stream(stream)))
+    return out
+
+
+def tcgs_bin_sort_workspace_size(P: int, capacity: int, num_tiles: int) -> int:
+    return int(_L().tcgs_bin_sort_workspace_size(int(P), int(capacity), int(num_tiles)))
+
+
+def tcgs_bin_sort(cam, mean2d, radius, depth, capacity: int, workspace=None, out=None, stream=None) -> dict:
+    c = _cam(cam)
+    P = mean2d.shape[0]
+    dev = mean2d.device
+    gw, gh = grid(c)
+    nt = gw * gh
+    ws_bytes = tcgs_bin_sort_workspace_size(P, capacity, nt)
+    if workspace is None:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    if out is None:
+        out = dict(ids_sorted=torch.empty(max(int(capacity), 1), dtype=torch.int32, device=dev),
+                   tile_ranges=torch.empty(nt, 2, dtype=torch.int32, device=dev),
+                   n_splats=torch.empty(1, dtype=torch.int64, device=dev),
+                   status=torch.empty(1, dtype=torch.int32, device=dev))
+    check("tcgs_bin_sort", _L().tcgs_bin_sort(
+        ctypes.byref(c), P, _ptr(mean2d, torch.float32, "mean2d"), _ptr(radius, torch.int32, "radius"),
+        _ptr(depth, torch.float32, "depth"), int(capacity), _ptr(workspace, None, "workspace"),
+        workspace.numel() * workspace.element_size(), _ptr(out["ids_sorted"], torch.int32),
+        _ptr(out["tile_ranges"], torch.int32), _ptr(out["n_splats"], torch.int64), _ptr(out["status"], torch.int32),
+        _stream(stream)))
+    return out
+
+
+def tcgs_render_fwd(cam, opts, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, bg=(0.0, 0.0, 0.0), out=None,
+                    stream=None) -> dict:
+    c = _cam(cam)
+    if not isinstance(opts, tcgs_render_opts):
+        opts = render_opts(**opts)
+    dev = mean2d.device
+    H, W = c.height, c.width
+    if out is None:
+        out = dict(img=torch.empty(3, H, W, device=dev), T_final=torch.empty(H, W, device=dev),
+                   n_contrib=torch.empty(H, W, dtype=torch.int32, device=dev))
+    bg3 = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    f = torch.float32
+    check("tcgs_render_fwd", _L().tcgs_render_fwd(
+        ctypes.byref(c), ctypes.byref(opts), _ptr(tile_ranges, torch.int32, "tile_ranges"),
+        _ptr(ids_sorted, torch.int32, "ids_sorted"), _ptr(mean2d, f, "mean2d"), _ptr(conic, f, "conic"),
+        _ptr(opacity, f, "opacity"), _ptr(rgb, f, "rgb"), ctypes.cast(bg3, ctypes.c_void_p),
+        _ptr(out["img"], f), _ptr(out["T_final"], f), _ptr(out["n_contrib"], torch.int32), _stream(stream)))
+    return out
+
+
+def tcgs_render_bwd(cam, opts, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, img, T_final, n_contrib,
+                    dL_dimg, bg=(0.0, 0.0, 0.0), grads=None, stream=None) -> dict:
+    c = _cam(cam)
+    if not isinstance(opts, tcgs_render_opts):
+        opts = render_opts(**opts)
+    P = mean2d.shape[0]
+    dev = mean2d.device
+    if grads is None:
+        grads = dict(dmean2d=torch.zeros(P, 2, device=dev), dconic=torch.zeros(P, 3, device=dev),
+                     dopacity=torch.zeros(P, device=dev), drgb=torch.zeros(P, 3, device=dev))
+    bg3 = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    f = torch.float32
+    check("tcgs_render_bwd", _L().tcgs_render_bwd(
+        ctypes.byref(c), ctypes.byref(opts), _ptr(tile_ranges, torch.int32, "tile_ranges"),
+        _ptr(ids_sorted, torch.int32, "ids_sorted"), _ptr(mean2d, f, "mean2d"), _ptr(conic, f, "conic"),
+        _ptr(opacity, f, "opacity"), _ptr(rgb, f, "rgb"), ctypes.cast(bg3, ctypes.c_void_p), _ptr(img, f, "img"),
+        _ptr(T_final, f, "T_final"), _ptr(n_contrib, torch.int32, "n_contrib"), _ptr(dL_dimg, f, "dL_dimg"),
+        _ptr(grads["dmean2d"], f), _ptr(grads["dconic"], f), _ptr(grads["dopacity"], f), _ptr(grads["drgb"], f),
+        _stream(stream)))
+    return grads
+
+
+def tcgs_frag2mat_beta(cam, precision, tile_ranges, ids_sorted, mean2d, conic, opacity, tiles, max_n,
+                       device_status=None, stream=None) -> torch.Tensor:
+    c = _cam(cam)
+    tiles = torch.as_tensor(tiles, dtype=torch.int32, device=mean2d.device).contiguous()
+    out = torch.empty(tiles.numel(), 256, int(max_n), device=mean2d.device)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    f = torch.float32
+    check("tcgs_frag2mat_beta", _L().tcgs_frag2mat_beta(
+        ctypes.byref(c), prec, _ptr(tile_ranges, torch.int32), _ptr(ids_sorted, torch.int32), _ptr(mean2d, f),
+        _ptr(conic, f), _ptr(opacity, f), tiles.numel(), _ptr(tiles, torch.int32), int(max_n), _ptr(out, f),
+        _ptr(device_status, torch.int32) if device_status is not None else None, _stream(stream)))
+    return out
+
+
+# ---------------------------------------------------------------- frame pipeline
+
+def scene_to_device(scene: dict, device="cuda") -> dict:
+    """Copy a ``scenes`` dict of numpy arrays to device tensors (float32)."""
+    out = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in scene.items()
+           if isinstance(v, np.ndarray)}
+    out["sh_degree"] = int(scene["sh_degree"])
+    return out
+
+
+class Renderer:
+    """Preallocated buffers for one camera, scene size and splat capacity; ``frame`` runs
+    project -> bin_sort -> render_fwd on the current stream with no host synchronisation."""
+
+    def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False):
+        self.cam = _cam(cam)
+        self.P, self.capacity = int(P), int(capacity)
+        dev = torch.device(device)
+        gw, gh = grid(self.cam)
+        self.num_tiles = gw * gh
+        H, W = self.cam.height, self.cam.width
+        self.proj = dict(mean2d=torch.empty(P, 2, device=dev), conic=torch.empty(P, 3, device=dev),
+                         depth=torch.empty(P, device=dev), radius=torch.empty(P, dtype=torch.int32, device=dev),
+                         rgb=torch.empty(P, 3, device=dev), tiles_touched=torch.empty(P, dtype=torch.int32, device=dev))
+        self.ws = torch.empty(tcgs_bin_sort_workspace_size(P, capacity, self.num_tiles), dtype=torch.uint8,
+                              device=dev)
+        self.bins = dict(ids_sorted=torch.empty(max(capacity, 1), dtype=torch.int32, device=dev),
+                         tile_ranges=torch.empty(self.num_tiles, 2, dtype=torch.int32, device=dev),
+                         n_splats=torch.zeros(1, dtype=torch.int64, device=dev),
+                         status=torch.zeros(1, dtype=torch.int32, device=dev))
+        self.out = dict(img=torch.empty(3, H, W, device=dev), T_final=torch.empty(H, W, device=dev),
+                        n_contrib=torch.empty(H, W, dtype=torch.int32, device=dev))
+        self.stats = torch.zeros(self.num_tiles, 4, dtype=torch.int32, device=dev) if stats else None
+        self.device_status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def project(self, scene: dict, stream=None):
+        return tcgs_project(self.cam, scene["means3"], scene["scales"], scene["quats"], scene["sh"],
+                            scene["sh_degree"], out=self.proj, stream=stream)
+
+    def bin_sort(self, stream=None):
+        return tcgs_bin_sort(self.cam, self.proj["mean2d"], self.proj["radius"], self.proj["depth"], self.capacity,
+                             workspace=self.ws, out=self.bins, stream=stream)
+
+    def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=False, bg=(0, 0, 0),
+               stream=None):
+        opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status)
+        return tcgs_render_fwd(self.cam, opts, self.bins["tile_ranges"], self.bins["ids_sorted"],
+                               self.proj["mean2d"], self.proj["conic"], opacity, self.proj["rgb"], bg=bg,
+                               out=self.out, stream=stream)
+
+    def frame(self, scene: dict, precision="tc_fp16_split", stream=None, **kw):
+        self.project(scene, stream)
+        self.bin_sort(stream)
+        return self.render(scene["opacity"], precision, stream=stream, **kw)
+
+
+# ---------------------------------------------------------------- autograd
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mean2d, conic, opacity, rgb, cam, tile_ranges, ids_sorted, precision, alpha_max, bg):
+        out = tcgs_render_fwd(cam, render_opts(precision, alpha_max), tile_ranges, ids_sorted, mean2d, conic,
+                              opacity, rgb, bg=bg)
+        ctx.cam, ctx.alpha_max, ctx.bg = cam, alpha_max, bg
+        ctx.save_for_backward(mean2d, conic, opacity, rgb, tile_ranges, ids_sorted, out["img"], out["T_final"],
+                              out["n_contrib"])
+        ctx.mark_non_differentiable(out["T_final"])
+        return out["img"], out["T_final"]
+
+    @staticmethod
+    def backward(ctx, g_img, g_T):
+        mean2d, conic, opacity, rgb, ranges, ids, img, T_final, n_contrib = ctx.saved_tensors
+        g = tcgs_render_bwd(ctx.cam, render_opts("fp32", ctx.alpha_max), ranges, ids, mean2d, conic, opacity, rgb,
+                            img, T_final, n_contrib, g_img.contiguous(), bg=ctx.bg)
+        return g["dmean2d"], g["dconic"], g["dopacity"], g["drgb"], None, None, None, None, None, None
+
+
+def rasterize(mean2d, conic, opacity, rgb, cam, tile_ranges, ids_sorted, precision="fp32", alpha_max=0.99,
+              bg=(0.0, 0.0, 0.0)):
+    """Differentiable alpha-blending stage: returns (img [3,H,W], T_final [H,W]); gradients flow
+    to mean2d, conic, opacity and rgb through the library's backward kernel."""
+    return _Rasterize.apply(mean2d, conic, opacity, rgb, _cam(cam), tile_ranges, ids_sorted, precision, alpha_max,
+                            tuple(bg))

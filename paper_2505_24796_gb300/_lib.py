@@ -1,0 +1,84 @@
+"""ctypes view of libtcgs.so (include/tcgs.h).  Argument marshalling only.
+
+Loading fails loudly when the library is missing and cannot be built: there is
+no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+c_int32, c_int64, c_float, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p,
+                                                 ctypes.c_size_t)
+
+TCGS_OK, TCGS_ERR_INVALID, TCGS_ERR_CUDA, TCGS_ERR_CAPACITY, TCGS_ERR_TIMEOUT, TCGS_ERR_UNSUPPORTED = range(6)
+TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS_TC_FP8 = range(4)
+PRECISIONS = {"fp32": TCGS_FP32, "tc_fp16": TCGS_TC_FP16, "tc_fp16_split": TCGS_TC_FP16_SPLIT, "tc_fp8": TCGS_TC_FP8}
+
+
+class tcgs_camera(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float), ("viewmat", c_float * 12), ("campos", c_float * 3), ("near_z", c_float),
+                ("tan_fovx", c_float), ("tan_fovy", c_float)]
+
+
+class tcgs_render_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("alpha_max", c_float), ("early_cull", c_int32), ("tile_stats", c_void_p),
+                ("device_status", c_void_p)]
+
+
+# name -> (restype, argtypes); the same names and order as include/tcgs.h
+P_CAM = ctypes.POINTER(tcgs_camera)
+P_OPT = ctypes.POINTER(tcgs_render_opts)
+V = c_void_p
+SIGNATURES = {
+    "tcgs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tcgs_version": (ctypes.c_int, []),
+    "tcgs_project": (c_int32, [P_CAM, c_int32, c_int32, V, V, V, V, V, V, V, V, V, V, V]),
+    "tcgs_bin_sort_workspace_size": (c_size_t, [c_int32, c_int64, c_int32]),
+    "tcgs_bin_sort": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
+    "tcgs_render_fwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V]),
+    "tcgs_render_bwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V]),
+    "tcgs_frag2mat_beta": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int32, V, c_int32, V, V, V]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load libtcgs.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_needed:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libtcgs.so not found at {_build.LIB}; build it with "
+                                   "paper_2505_24796_gb300.build.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class TcgsError(RuntimeError):
+    def __init__(self, name, code):
+        msg = load(False).tcgs_status_string(code).decode()
+        super().__init__(f"{name} failed: {msg} (status {code})")
+        self.code = code
+
+
+def check(name: str, code: int) -> None:
+    if code != TCGS_OK:
+        raise TcgsError(name, code)

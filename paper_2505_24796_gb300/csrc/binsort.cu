@@ -1,0 +1,414 @@
+// binsort.cu -- sorting stage (Sec. 3.1, Eq. 3): splats, per-tile depth order, tile ranges.
+//
+// The paper orders splats by a radix sort of (tile, depth) keys.  We run the same LSD
+// radix sort but hoist its depth digits in front of the duplication:
+//   1. depth keys of the P Gaussians, stable LSD radix sort (4 passes of 8 bits) -> order;
+//   2. exclusive scan of the tile counts in that order -> splat offsets, N, capacity check;
+//   3. duplication in depth order: splat = (tile id, Gaussian id);
+//   4. stable LSD radix sort of the splats by tile id (ceil(log2 tiles / 8) passes);
+//   5. tile ranges from adjacent tile-id changes.
+// Because every pass is stable and duplication preserves the depth order, the result is the
+// (tile, depth, id) order of the 64-bit-key sort, while only 1-2 passes touch the N splats.
+//
+// Radix sort design (per pass): a fixed grid of G blocks; block b owns one contiguous key
+// range.  hist: per-block 256-bin digit counts (+ global digit totals).  scan: one block per
+// digit turns the counts into global output offsets.  scatter: each warp ranks its 32-key
+// rounds with __match_any_sync, warps and tiles are chained in order, so the pass is stable.
+// No block ever waits on another block.
+#include "common.cuh"
+
+namespace tcgs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;                       // keys per thread per tile
+constexpr int kTileItems = kThreads * kItems;   // 2048 keys per tile
+constexpr int kRadix = 256;
+constexpr int kMaxBlocks = 1024;
+constexpr int kScanBlocks = 1024;
+
+__device__ __forceinline__ uint32_t load_n(uint32_t n_host, const uint32_t* n_dev) {
+    return n_dev ? *n_dev : n_host;
+}
+
+__device__ __forceinline__ void block_range(uint32_t n, int G, uint32_t& lo, uint32_t& hi) {
+    uint32_t tiles = (n + kTileItems - 1) / kTileItems;
+    uint32_t per = (tiles + G - 1) / G;
+    uint64_t l = (uint64_t)blockIdx.x * per * kTileItems;
+    uint64_t h = l + (uint64_t)per * kTileItems;
+    lo = (uint32_t)(l < n ? l : n);
+    hi = (uint32_t)(h < n ? h : n);
+}
+
+// Exclusive scan over a block of NT threads; returns the thread's exclusive prefix and the total.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* warp_sums, T& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = NT / 32;
+        T w = lane < NW ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    T before = warp > 0 ? warp_sums[warp - 1] : T(0);
+    total = warp_sums[NT / 32 - 1];
+    __syncthreads();
+    return before + v - x;
+}
+
+// ---------------------------------------------------------------- radix sort passes
+
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
+                                                         const uint32_t* n_dev, int shift, int G,
+                                                         uint32_t* __restrict__ hist,
+                                                         uint32_t* __restrict__ digit_total) {
+    __shared__ uint32_t h[kWarps][kRadix];
+    const int t = threadIdx.x, warp = t >> 5;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) h[w][t] = 0;
+    __syncthreads();
+    uint32_t lo, hi;
+    block_range(load_n(n_host, n_dev), G, lo, hi);
+    for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & 0xFFu], 1u);
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += h[w][t];
+    hist[(size_t)t * G + blockIdx.x] = s;
+    if (s) atomicAdd(&digit_total[t], s);
+}
+
+// Block d turns row d of hist (the G per-block counts of digit d) into global offsets:
+// offset(d, b) = sum_{d' < d} total(d') + sum_{b' < b} count(d, b').
+__global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ hist,
+                                                         const uint32_t* __restrict__ digit_total,
+                                                         uint32_t* __restrict__ digit_total_next, int G) {
+    __shared__ uint32_t ws[kWarps];
+    const int d = blockIdx.x, t = threadIdx.x;
+    uint32_t tot;
+    uint32_t mine = t < d ? digit_total[t] : 0u;
+    // base = sum of totals of smaller digits (reuse the scan for a reduction)
+    block_exclusive_scan<uint32_t, kThreads>(mine, ws, tot);
+    uint32_t run = tot;
+    uint32_t* row = hist + (size_t)d * G;
+    for (int b0 = 0; b0 < G; b0 += kThreads) {
+        int b = b0 + t;
+        uint32_t x = b < G ? row[b] : 0u;
+        uint32_t chunk;
+        uint32_t ex = block_exclusive_scan<uint32_t, kThreads>(x, ws, chunk);
+        if (b < G) row[b] = run + ex;
+        run += chunk;
+    }
+    if (d == 0) digit_total_next[t] = 0u;
+}
+
+__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
+                                                            const uint32_t* __restrict__ vals_in,
+                                                            uint32_t* __restrict__ keys_out,
+                                                            uint32_t* __restrict__ vals_out, uint32_t n_host,
+                                                            const uint32_t* n_dev, int shift, int G,
+                                                            const uint32_t* __restrict__ offsets) {
+    __shared__ uint32_t wcnt[kWarps][kRadix];
+    __shared__ uint32_t boff[kRadix];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    uint32_t lo, hi;
+    block_range(load_n(n_host, n_dev), G, lo, hi);
+    boff[t] = offsets[(size_t)t * G + blockIdx.x];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (uint32_t tile = lo; tile < hi; tile += kTileItems) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) wcnt[w][t] = 0;
+        __syncthreads();
+        uint32_t k[kItems], v[kItems], rank[kItems];
+        uint32_t dg[kItems];
+        const uint32_t base = tile + (uint32_t)warp * (32 * kItems);
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            uint32_t i = base + r * 32 + lane;
+            bool valid = i < hi;
+            k[r] = valid ? keys_in[i] : 0u;
+            v[r] = valid ? vals_in[i] : 0u;
+            uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u | lane);
+            dg[r] = d;
+            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = 0;
+            if (valid) before = wcnt[warp][d];
+            __syncwarp();
+            if (valid && lane == 31 - __clz(peers)) wcnt[warp][d] = before + __popc(peers);
+            __syncwarp();
+            rank[r] = before + __popc(peers & lt_mask);
+        }
+        __syncthreads();
+        uint32_t run = boff[t];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t c = wcnt[w][t];
+            wcnt[w][t] = run;
+            run += c;
+        }
+        boff[t] = run;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            if (dg[r] < 0x100u) {
+                uint32_t pos = wcnt[warp][dg[r]] + rank[r];
+                keys_out[pos] = k[r];
+                vals_out[pos] = v[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- binning kernels
+
+__device__ __forceinline__ uint32_t orderable_bits(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, const float* __restrict__ mean2d,
+                                                       const int32_t* __restrict__ radius,
+                                                       const float* __restrict__ depth, uint32_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ vals, uint32_t* __restrict__ counts,
+                                                       uint32_t* __restrict__ ranges, int n_range_words,
+                                                       uint32_t* __restrict__ digit_total0) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0) digit_total0[threadIdx.x] = 0u;
+    if (i < n_range_words) ranges[i] = 0u;
+    if (i >= P) return;
+    float2 m = reinterpret_cast<const float2*>(mean2d)[i];
+    Rect rc = tile_rect(m.x, m.y, radius[i], cam.grid_w, cam.grid_h);
+    uint32_t c = rect_count(rc);
+    counts[i] = c;
+    keys[i] = c ? orderable_bits(depth[i]) : 0xFFFFFFFFu;
+    vals[i] = (uint32_t)i;
+}
+
+// block sums of counts[order[i]] over contiguous ranges
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ counts,
+                                                          const uint32_t* __restrict__ order, uint32_t P, int G2,
+                                                          unsigned long long* __restrict__ block_sums) {
+    __shared__ unsigned long long ws[kWarps];
+    uint32_t per = (P + G2 - 1) / G2;
+    uint64_t lo = (uint64_t)blockIdx.x * per, hi = lo + per;
+    if (hi > P) hi = P;
+    unsigned long long s = 0;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += kThreads) s += counts[order[i]];
+    unsigned long long tot;
+    block_exclusive_scan<unsigned long long, kThreads>(s, ws, tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* __restrict__ block_sums, int G2,
+                                                   int64_t capacity, int64_t* __restrict__ n_splats,
+                                                   int32_t* __restrict__ status, uint32_t* __restrict__ n_u32) {
+    __shared__ unsigned long long ws[32];
+    int t = threadIdx.x;
+    unsigned long long x = t < G2 ? block_sums[t] : 0ull;
+    unsigned long long tot;
+    unsigned long long ex = block_exclusive_scan<unsigned long long, 1024>(x, ws, tot);
+    if (t < G2) block_sums[t] = ex;
+    if (t == 0) {
+        *n_splats = (int64_t)tot;
+        bool ok = tot <= (unsigned long long)capacity;
+        *status = ok ? TCGS_OK : TCGS_ERR_CAPACITY;
+        *n_u32 = ok ? (uint32_t)tot : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_final(const uint32_t* __restrict__ counts,
+                                                         const uint32_t* __restrict__ order, uint32_t P, int G2,
+                                                         const unsigned long long* __restrict__ block_sums,
+                                                         uint32_t* __restrict__ offsets,
+                                                         const uint32_t* __restrict__ n_u32) {
+    __shared__ unsigned long long ws[kWarps];
+    uint32_t per = (P + G2 - 1) / G2;
+    uint64_t lo = (uint64_t)blockIdx.x * per, hi = lo + per;
+    if (hi > P) hi = P;
+    bool ok = *n_u32 > 0;  // zero splats or capacity exceeded: nothing to place
+    unsigned long long run = block_sums[blockIdx.x];
+    for (uint64_t c0 = lo; c0 < hi; c0 += kThreads) {
+        uint64_t i = c0 + threadIdx.x;
+        unsigned long long x = i < hi ? counts[order[i]] : 0ull;
+        unsigned long long tot;
+        unsigned long long ex = block_exclusive_scan<unsigned long long, kThreads>(x, ws, tot);
+        if (ok && i < hi) offsets[i] = (uint32_t)(run + ex);
+        run += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t P, const uint32_t* __restrict__ order,
+                                                        const uint32_t* __restrict__ offsets,
+                                                        const uint32_t* __restrict__ counts,
+                                                        const float* __restrict__ mean2d,
+                                                        const int32_t* __restrict__ radius,
+                                                        uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
+                                                        const uint32_t* __restrict__ n_u32) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P || *n_u32 == 0u) return;
+    uint32_t g = order[i];
+    if (counts[g] == 0u) return;
+    float2 m = reinterpret_cast<const float2*>(mean2d)[g];
+    Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
+    uint32_t o = offsets[i];
+    for (int ty = rc.y0; ty <= rc.y1; ++ty)
+        for (int tx = rc.x0; tx <= rc.x1; ++tx) {
+            tile_keys[o] = (uint32_t)(ty * cam.grid_w + tx);
+            vals[o] = g;
+            ++o;
+        }
+}
+
+__global__ void __launch_bounds__(kThreads) k_ranges(const uint32_t* __restrict__ tile_keys,
+                                                     const uint32_t* __restrict__ n_u32,
+                                                     uint32_t* __restrict__ ranges) {
+    uint32_t n = *n_u32;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t t = tile_keys[i];
+        if (i == 0 || tile_keys[i - 1] != t) ranges[2 * t] = i;
+        if (i == n - 1 || tile_keys[i + 1] != t) ranges[2 * t + 1] = i + 1;
+    }
+}
+
+// ---------------------------------------------------------------- workspace
+
+struct Workspace {
+    uint32_t *dk_a, *dv_a, *dk_b, *dv_b;   // depth sort ping-pong (P)
+    uint32_t *counts, *offsets;            // P
+    unsigned long long* block_sums;        // kScanBlocks
+    uint32_t* hist;                        // 256 * kMaxBlocks
+    uint32_t* digit_total;                 // 2 * 256
+    uint32_t* n_u32;                       // 1 (+ padding)
+    uint32_t *sk_a, *sk_b, *sv_b;          // splat sort buffers (capacity)
+    size_t bytes;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline Workspace layout(char* base, int64_t P, int64_t cap) {
+    Workspace w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+    w.dk_a = (uint32_t*)take(4 * P); w.dv_a = (uint32_t*)take(4 * P);
+    w.dk_b = (uint32_t*)take(4 * P); w.dv_b = (uint32_t*)take(4 * P);
+    w.counts = (uint32_t*)take(4 * P); w.offsets = (uint32_t*)take(4 * P);
+    w.block_sums = (unsigned long long*)take(8 * kScanBlocks);
+    w.hist = (uint32_t*)take(4 * (size_t)kRadix * kMaxBlocks);
+    w.digit_total = (uint32_t*)take(4 * 2 * kRadix);
+    w.n_u32 = (uint32_t*)take(256);
+    w.sk_a = (uint32_t*)take(4 * cap); w.sk_b = (uint32_t*)take(4 * cap); w.sv_b = (uint32_t*)take(4 * cap);
+    w.bytes = off;
+    return w;
+}
+
+inline int sort_blocks(int64_t n) {
+    int64_t tiles = (n + kTileItems - 1) / kTileItems;
+    if (tiles < 1) tiles = 1;
+    return (int)(tiles < kMaxBlocks ? tiles : kMaxBlocks);
+}
+
+// One LSD pass; digit totals ping-pong between two 256-word buffers (the scan of a pass zeroes
+// the buffer the next pass accumulates into).
+inline void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n_host,
+                       const uint32_t* n_dev, int shift, int G, const Workspace& w, int pass, cudaStream_t s) {
+    uint32_t* tot = w.digit_total + (pass & 1) * kRadix;
+    uint32_t* nxt = w.digit_total + ((pass + 1) & 1) * kRadix;
+    k_radix_hist<<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, G, w.hist, tot);
+    k_radix_scan<<<kRadix, kThreads, 0, s>>>(w.hist, tot, nxt, G);
+    k_radix_scatter<<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, G, w.hist);
+}
+
+}  // namespace
+}  // namespace tcgs
+
+extern "C" size_t tcgs_bin_sort_workspace_size(int32_t P, int64_t splat_capacity, int32_t num_tiles) {
+    (void)num_tiles;
+    if (P < 0 || splat_capacity < 0) return 0;
+    return tcgs::layout(nullptr, P, splat_capacity).bytes;
+}
+
+extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, const int32_t* radius,
+                                     const float* depth, int64_t splat_capacity, void* workspace, size_t ws_bytes,
+                                     uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_splats,
+                                     int32_t* status, tcgs_stream stream) {
+    using namespace tcgs;
+    if (!valid_camera(cam) || P < 0 || splat_capacity < 0 || splat_capacity > (int64_t)0xFFFFFFFFu)
+        return TCGS_ERR_INVALID;
+    if (!tile_ranges || !n_splats || !status || (P > 0 && (!mean2d || !radius || !depth)) || !workspace ||
+        (splat_capacity > 0 && !ids_sorted))
+        return TCGS_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) || (reinterpret_cast<uintptr_t>(mean2d) & 7))
+        return TCGS_ERR_INVALID;
+    DevCamera dc = make_dev_camera(*cam);
+    const int num_tiles = dc.grid_w * dc.grid_h;
+    Workspace w = layout((char*)workspace, P, splat_capacity);
+    if (ws_bytes < w.bytes) return TCGS_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // keys, counts, range clearing, digit totals of pass 0
+    int n_init = P > 2 * num_tiles ? P : 2 * num_tiles;
+    if (n_init < kThreads) n_init = kThreads;
+    k_bin_keys<<<(n_init + kThreads - 1) / kThreads, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, w.dk_a, w.dv_a,
+                                                                       w.counts, tile_ranges, 2 * num_tiles,
+                                                                       w.digit_total);
+    TCGS_CHECK_LAUNCH();
+    // 1. depth order (4 passes; the result returns to the a-buffers)
+    int pass = 0;
+    if (P > 0) {
+        int Gp = sort_blocks(P);
+        for (int sh = 0; sh < 32; sh += 8, ++pass) {
+            bool even = (pass & 1) == 0;
+            radix_pass(even ? w.dk_a : w.dk_b, even ? w.dv_a : w.dv_b, even ? w.dk_b : w.dk_a,
+                       even ? w.dv_b : w.dv_a, (uint32_t)P, nullptr, sh, Gp, w, pass, s);
+        }
+        TCGS_CHECK_LAUNCH();
+    }
+    const uint32_t* order = w.dv_a;
+    // 2. offsets, N, capacity check
+    int G2 = P < kScanBlocks * 256 ? (P + 255) / 256 : kScanBlocks;
+    if (G2 < 1) G2 = 1;
+    if (P > 0) k_scan_reduce<<<G2, kThreads, 0, s>>>(w.counts, order, (uint32_t)P, G2, w.block_sums);
+    else cudaMemsetAsync(w.block_sums, 0, 8, s);
+    k_scan_top<<<1, 1024, 0, s>>>(w.block_sums, G2, splat_capacity, n_splats, status, w.n_u32);
+    if (P > 0)
+        k_scan_final<<<G2, kThreads, 0, s>>>(w.counts, order, (uint32_t)P, G2, w.block_sums, w.offsets, w.n_u32);
+    TCGS_CHECK_LAUNCH();
+    if (splat_capacity == 0 || P == 0) return TCGS_OK;
+    // 3. duplication into the buffer the first tile pass reads
+    int tile_bits = 0;
+    while ((1 << tile_bits) < num_tiles) ++tile_bits;
+    int tpasses = tile_bits <= 8 ? 1 : (tile_bits <= 16 ? 2 : 3);
+    uint32_t* kbuf[2] = {w.sk_a, w.sk_b};
+    uint32_t* vbuf[2] = {ids_sorted, w.sv_b};
+    int src = (tpasses & 1) ? 1 : 0;
+    k_duplicate<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts,
+                                                                  mean2d, radius, kbuf[src], vbuf[src], w.n_u32);
+    TCGS_CHECK_LAUNCH();
+    // 4. stable sort by tile id
+    int Gs = sort_blocks(splat_capacity);
+    for (int tp = 0; tp < tpasses; ++tp, ++pass) {
+        radix_pass(kbuf[src], vbuf[src], kbuf[src ^ 1], vbuf[src ^ 1], 0u, w.n_u32, 8 * tp, Gs, w, pass, s);
+        src ^= 1;
+    }
+    TCGS_CHECK_LAUNCH();
+    // 5. ranges
+    int Gr = sort_blocks(splat_capacity) * 4;
+    k_ranges<<<Gr, kThreads, 0, s>>>(kbuf[src], w.n_u32, tile_ranges);
+    TCGS_CHECK_LAUNCH();
+    return TCGS_OK;
+}

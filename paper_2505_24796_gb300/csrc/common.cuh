@@ -1,0 +1,96 @@
+// common.cuh -- shared device helpers of libtcgs (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "tcgs.h"
+
+namespace tcgs {
+
+constexpr int kTile = 16;            // tile edge in pixels (Sec. 4.3: 16 x 16 tiles)
+constexpr float kCullAlpha = 1.0f / 255.0f;   // Eq. (5)
+constexpr float kTmin = 1e-4f;       // termination threshold of Algorithm 1
+constexpr float kLog2e = 1.4426950408889634f;
+// -ln(255) (EarlyCull, Sec. 4.1) and the same threshold in log2 units
+constexpr float kBetaCull = -5.541263545158426f;
+constexpr float kBeta2Cull = -7.994353436858858f;   // -log2(255)
+
+struct DevCamera {
+    int width, height, grid_w, grid_h;
+    float fx, fy, cx, cy;
+    float R[9], t[3];
+    float campos[3];
+    float near_z, limx, limy;
+};
+
+inline DevCamera make_dev_camera(const tcgs_camera& c) {
+    DevCamera d;
+    d.width = c.width;
+    d.height = c.height;
+    d.grid_w = (c.width + kTile - 1) / kTile;
+    d.grid_h = (c.height + kTile - 1) / kTile;
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) d.R[3 * i + k] = c.viewmat[4 * i + k];
+        d.t[i] = c.viewmat[4 * i + 3];
+        d.campos[i] = c.campos[i];
+    }
+    d.near_z = c.near_z;
+    float tx = c.tan_fovx > 0.f ? c.tan_fovx : 0.5f * (float)c.width / c.fx;
+    float ty = c.tan_fovy > 0.f ? c.tan_fovy : 0.5f * (float)c.height / c.fy;
+    d.limx = 1.3f * tx;
+    d.limy = 1.3f * ty;
+    return d;
+}
+
+inline bool valid_camera(const tcgs_camera* c) {
+    return c && c->width > 0 && c->height > 0 && c->fx > 0.f && c->fy > 0.f && c->width <= (1 << 20) &&
+           c->height <= (1 << 20);
+}
+
+// Tile rectangle of a projected Gaussian, exact for any finite float mean and integer radius:
+// x tiles [floor((mx - r) / 16), floor((mx + r) / 16)] clipped to the grid.  floor(mx) is exact
+// in float, so floor((mx -+ r) / 16) = floor_div(floor(mx) -+ r, 16) in 64-bit integers.
+struct Rect { int x0, x1, y0, y1; };   // inclusive bounds; empty when x1 < x0 or y1 < y0
+
+__device__ __forceinline__ long long floor_div16(long long v) { return v >= 0 ? v / 16 : -((-v + 15) / 16); }
+
+__device__ __forceinline__ Rect tile_rect(float mx, float my, int r, int gw, int gh) {
+    Rect o;
+    const float lim = 4.0e18f;
+    if (!(fabsf(mx) < lim) || !(fabsf(my) < lim) || r <= 0) { o.x0 = o.y0 = 0; o.x1 = o.y1 = -1; return o; }
+    long long fx = (long long)floorf(mx), fy = (long long)floorf(my);
+    long long lx = floor_div16(fx - r), hx = floor_div16(fx + r);
+    long long ly = floor_div16(fy - r), hy = floor_div16(fy + r);
+    lx = lx < 0 ? 0 : lx; ly = ly < 0 ? 0 : ly;
+    hx = hx > gw - 1 ? gw - 1 : hx; hy = hy > gh - 1 ? gh - 1 : hy;
+    if (hx < lx || hy < ly) { o.x0 = o.y0 = 0; o.x1 = o.y1 = -1; return o; }
+    o.x0 = (int)lx; o.x1 = (int)hx; o.y0 = (int)ly; o.y1 = (int)hy;
+    return o;
+}
+
+__device__ __forceinline__ uint32_t rect_count(const Rect& r) {
+    if (r.x1 < r.x0 || r.y1 < r.y0) return 0u;
+    return (uint32_t)(r.x1 - r.x0 + 1) * (uint32_t)(r.y1 - r.y0 + 1);
+}
+
+// 2^x on the SFU (PTX ex2.approx.ftz.f32).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void set_status(int32_t* st, int code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+}  // namespace tcgs
+
+#define TCGS_CHECK_LAUNCH()                                  \
+    do {                                                     \
+        cudaError_t e_ = cudaGetLastError();                 \
+        if (e_ != cudaSuccess) return TCGS_ERR_CUDA;         \
+    } while (0)

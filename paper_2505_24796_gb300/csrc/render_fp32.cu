@@ -1,0 +1,293 @@
+// render_fp32.cu -- conditional alpha-blending on CUDA cores (Algorithm 1, Eq. 4-6): the
+// FP32 baseline the tensor-core path is measured against, and the backward replay.
+//
+// Forward: one CTA of 256 threads per 16 x 16 tile, one thread per pixel.  The tile's sorted
+// list is walked in batches of 256 Gaussians staged in shared memory (one coalesced-by-id
+// gather per thread); each thread runs Algorithm 1 on the batch; a block-wide count of
+// finished pixels ends the walk early.
+#include "common.cuh"
+
+namespace tcgs {
+namespace {
+
+constexpr int kFwdThreads = 256;
+
+struct FwdParams {
+    DevCamera cam;
+    const uint32_t* ranges;
+    const uint32_t* ids;
+    const float* mean2d;
+    const float* conic;
+    const float* opacity;
+    const float* rgb;
+    float bg[3];
+    float alpha_max;
+    int early_cull;
+    float* img;
+    float* T_final;
+    uint32_t* n_contrib;
+    uint32_t* stats;
+};
+
+__global__ void __launch_bounds__(kFwdThreads) k_render_fp32(FwdParams p) {
+    __shared__ float2 s_xy[kFwdThreads];
+    __shared__ float4 s_co[kFwdThreads];   // sigma11, sigma12, sigma22, opacity
+    __shared__ float4 s_rgb[kFwdThreads];  // r, g, b, ln(opacity)
+    const int tile = blockIdx.x;
+    const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
+    const int t = threadIdx.x;
+    const int px_i = tx * kTile + (t & 15), py_i = ty * kTile + (t >> 4);
+    const bool inside = px_i < p.cam.width && py_i < p.cam.height;
+    const float px = px_i + 0.5f, py = py_i + 0.5f;
+    const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0, n_eval = end - start, n_blend = 0;
+    bool done = !inside;
+    uint32_t walked = 0;
+    for (uint32_t b0 = start; b0 < end; b0 += kFwdThreads) {
+        if (__syncthreads_count(done) == kFwdThreads) break;
+        uint32_t idx = b0 + t;
+        if (idx < end) {
+            uint32_t g = p.ids[idx];
+            float2 m = reinterpret_cast<const float2*>(p.mean2d)[g];
+            float o = p.opacity[g];
+            s_xy[t] = m;
+            s_co[t] = make_float4(p.conic[3 * g], p.conic[3 * g + 1], p.conic[3 * g + 2], o);
+            s_rgb[t] = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], p.early_cull ? __logf(o) : 0.f);
+        }
+        __syncthreads();
+        uint32_t nb = end - b0 < (uint32_t)kFwdThreads ? end - b0 : (uint32_t)kFwdThreads;
+        walked += nb;
+        for (uint32_t j = 0; j < nb && !done; ++j) {
+            float2 m = s_xy[j];
+            float4 co = s_co[j];
+            float dx = m.x - px, dy = m.y - py;
+            float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+            if (p.early_cull && power + s_rgb[j].w < kBetaCull) continue;   // Sec. 4.1
+            float alpha = fminf(p.alpha_max, co.w * expf(power));
+            if (alpha < kCullAlpha) continue;                                  // Eq. (5)
+            float Tn = fmaf(-alpha, T, T);                                     // T - alpha T
+            if (Tn < kTmin) {                                                  // Algorithm 1: terminate
+                done = true;
+                n_eval = b0 + j + 1 - start;
+                break;
+            }
+            float4 c = s_rgb[j];
+            float w = alpha * T;
+            C0 += c.x * w; C1 += c.y * w; C2 += c.z * w;
+            T = Tn;
+            last = b0 + j + 1 - start;
+            ++n_blend;
+        }
+    }
+    if (inside) {
+        size_t pix = (size_t)py_i * p.cam.width + px_i;
+        size_t plane = (size_t)p.cam.width * p.cam.height;
+        p.img[pix] = C0 + T * p.bg[0];
+        p.img[plane + pix] = C1 + T * p.bg[1];
+        p.img[2 * plane + pix] = C2 + T * p.bg[2];
+        p.T_final[pix] = T;
+        p.n_contrib[pix] = last;
+    }
+    if (p.stats) {
+        __shared__ unsigned long long s_acc[3];
+        if (t < 3) s_acc[t] = 0ull;
+        __syncthreads();
+        if (inside) {
+            atomicAdd(&s_acc[0], (unsigned long long)n_blend);
+            atomicAdd(&s_acc[1], (unsigned long long)(n_eval - n_blend));
+        }
+        __syncthreads();
+        if (t == 0) {
+            atomicAdd(&p.stats[4 * tile + 0], (uint32_t)s_acc[0]);
+            atomicAdd(&p.stats[4 * tile + 1], (uint32_t)s_acc[1]);
+            atomicAdd(&p.stats[4 * tile + 2], walked * (uint32_t)kFwdThreads);
+            atomicAdd(&p.stats[4 * tile + 3], end - start);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- backward
+//
+// One CTA per tile, one thread per pixel.  Each pixel replays its fragments 0 .. n_contrib-1
+// front to back with the forward's FP32 alpha arithmetic, so T_j matches the forward bit for
+// bit; the colour blended after fragment j is img - bg T_final - (prefix up to j).  Per
+// Gaussian, the 9 gradient terms of a warp's pixels are summed with shuffles before one lane
+// issues the atomics.
+
+struct BwdParams {
+    DevCamera cam;
+    const uint32_t* ranges;
+    const uint32_t* ids;
+    const float* mean2d;
+    const float* conic;
+    const float* opacity;
+    const float* rgb;
+    float bg[3];
+    float alpha_max;
+    int early_cull;
+    const float* img;
+    const float* T_final;
+    const uint32_t* n_contrib;
+    const float* dL_dimg;
+    float* dmean2d;
+    float* dconic;
+    float* dopacity;
+    float* drgb;
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
+    __shared__ float2 s_xy[kFwdThreads];
+    __shared__ float4 s_co[kFwdThreads];
+    __shared__ float4 s_rgb[kFwdThreads];
+    __shared__ uint32_t s_id[kFwdThreads];
+    __shared__ uint32_t s_max;
+    const int tile = blockIdx.x;
+    const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
+    const int t = threadIdx.x, lane = t & 31;
+    const int px_i = tx * kTile + (t & 15), py_i = ty * kTile + (t >> 4);
+    const bool inside = px_i < p.cam.width && py_i < p.cam.height;
+    const float px = px_i + 0.5f, py = py_i + 0.5f;
+    const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
+
+    uint32_t nc = 0;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f, Tf = 1.f;
+    if (inside) {
+        size_t pix = (size_t)py_i * p.cam.width + px_i;
+        size_t plane = (size_t)p.cam.width * p.cam.height;
+        nc = p.n_contrib[pix];
+        Tf = p.T_final[pix];
+        g0 = p.dL_dimg[pix]; g1 = p.dL_dimg[plane + pix]; g2 = p.dL_dimg[2 * plane + pix];
+        // colour still to come after the current fragment, initially everything blended
+        R0 = p.img[pix] - Tf * p.bg[0];
+        R1 = p.img[plane + pix] - Tf * p.bg[1];
+        R2 = p.img[2 * plane + pix] - Tf * p.bg[2];
+    }
+    if (t == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, nc);
+    __syncthreads();
+    const uint32_t span = s_max;
+    float T = 1.f;
+    for (uint32_t b0 = 0; b0 < span; b0 += kFwdThreads) {
+        __syncthreads();
+        uint32_t idx = start + b0 + t;
+        if (idx < end) {
+            uint32_t g = p.ids[idx];
+            s_id[t] = g;
+            s_xy[t] = reinterpret_cast<const float2*>(p.mean2d)[g];
+            s_co[t] = make_float4(p.conic[3 * g], p.conic[3 * g + 1], p.conic[3 * g + 2], p.opacity[g]);
+            s_rgb[t] = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], 0.f);
+        }
+        __syncthreads();
+        uint32_t nb = span - b0 < (uint32_t)kFwdThreads ? span - b0 : (uint32_t)kFwdThreads;
+        for (uint32_t j = 0; j < nb; ++j) {
+            float dm0 = 0.f, dm1 = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dop = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
+            bool contrib = false;
+            if (b0 + j < nc) {
+                float2 m = s_xy[j];
+                float4 co = s_co[j];
+                float dx = m.x - px, dy = m.y - py;
+                float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+                float G = expf(power);
+                float raw = co.w * G;
+                float alpha = fminf(p.alpha_max, raw);
+                bool early = p.early_cull && power + __logf(co.w) < kBetaCull;   // same test as the forward
+                if (!early && alpha >= kCullAlpha) {
+                    contrib = true;
+                    float4 c = s_rgb[j];
+                    float w = alpha * T;
+                    dr0 = w * g0; dr1 = w * g1; dr2 = w * g2;
+                    R0 -= c.x * w; R1 -= c.y * w; R2 -= c.z * w;
+                    float ia = 1.f / (1.f - alpha);
+                    float dL_da = g0 * (c.x * T - (R0 + Tf * p.bg[0]) * ia) +
+                                  g1 * (c.y * T - (R1 + Tf * p.bg[1]) * ia) +
+                                  g2 * (c.z * T - (R2 + Tf * p.bg[2]) * ia);
+                    if (raw <= p.alpha_max) {
+                        float dL_dp = dL_da * alpha;
+                        dop = dL_da * G;
+                        dm0 = -dL_dp * (co.x * dx + co.y * dy);
+                        dm1 = -dL_dp * (co.y * dx + co.z * dy);
+                        dc0 = -0.5f * dL_dp * dx * dx;
+                        dc1 = -dL_dp * dx * dy;
+                        dc2 = -0.5f * dL_dp * dy * dy;
+                    }
+                    T = fmaf(-alpha, T, T);
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                dm0 = warp_sum(dm0); dm1 = warp_sum(dm1);
+                dc0 = warp_sum(dc0); dc1 = warp_sum(dc1); dc2 = warp_sum(dc2);
+                dop = warp_sum(dop);
+                dr0 = warp_sum(dr0); dr1 = warp_sum(dr1); dr2 = warp_sum(dr2);
+                if (lane == 0) {
+                    uint32_t g = s_id[j];
+                    atomicAdd(&p.dmean2d[2 * g], dm0); atomicAdd(&p.dmean2d[2 * g + 1], dm1);
+                    atomicAdd(&p.dconic[3 * g], dc0); atomicAdd(&p.dconic[3 * g + 1], dc1);
+                    atomicAdd(&p.dconic[3 * g + 2], dc2);
+                    atomicAdd(&p.dopacity[g], dop);
+                    atomicAdd(&p.drgb[3 * g], dr0); atomicAdd(&p.drgb[3 * g + 1], dr1);
+                    atomicAdd(&p.drgb[3 * g + 2], dr2);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace tcgs
+
+namespace tcgs {
+tcgs_status launch_render_fp32(const tcgs_camera* cam, const tcgs_render_opts* opts, const uint32_t* tile_ranges,
+                               const uint32_t* ids_sorted, const float* mean2d, const float* conic,
+                               const float* opacity, const float* rgb, const float* bg3, float* img, float* T_final,
+                               uint32_t* n_contrib, cudaStream_t s) {
+    FwdParams p;
+    p.cam = make_dev_camera(*cam);
+    p.ranges = tile_ranges; p.ids = ids_sorted; p.mean2d = mean2d; p.conic = conic; p.opacity = opacity;
+    p.rgb = rgb;
+    for (int i = 0; i < 3; ++i) p.bg[i] = bg3 ? bg3[i] : 0.f;
+    p.alpha_max = opts->alpha_max;
+    p.early_cull = opts->early_cull;
+    p.img = img; p.T_final = T_final; p.n_contrib = n_contrib; p.stats = opts->tile_stats;
+    int tiles = p.cam.grid_w * p.cam.grid_h;
+    k_render_fp32<<<tiles, kFwdThreads, 0, s>>>(p);
+    TCGS_CHECK_LAUNCH();
+    return TCGS_OK;
+}
+}  // namespace tcgs
+
+extern "C" tcgs_status tcgs_render_bwd(const tcgs_camera* cam, const tcgs_render_opts* opts,
+                                       const uint32_t* tile_ranges, const uint32_t* ids_sorted, const float* mean2d,
+                                       const float* conic, const float* opacity, const float* rgb, const float* bg3,
+                                       const float* img, const float* T_final, const uint32_t* n_contrib,
+                                       const float* dL_dimg, float* dmean2d, float* dconic, float* dopacity,
+                                       float* drgb, tcgs_stream stream) {
+    using namespace tcgs;
+    if (!valid_camera(cam) || !opts || !tile_ranges || !ids_sorted || !mean2d || !conic || !opacity || !rgb ||
+        !img || !T_final || !n_contrib || !dL_dimg || !dmean2d || !dconic || !dopacity || !drgb)
+        return TCGS_ERR_INVALID;
+    if (!(opts->alpha_max > 0.f && opts->alpha_max <= 1.f)) return TCGS_ERR_INVALID;
+    if (opts->alpha_max >= 1.f) return TCGS_ERR_INVALID;  // 1 / (1 - alpha) must stay finite
+    if (reinterpret_cast<uintptr_t>(mean2d) & 7) return TCGS_ERR_INVALID;
+    BwdParams p;
+    p.cam = make_dev_camera(*cam);
+    p.ranges = tile_ranges; p.ids = ids_sorted; p.mean2d = mean2d; p.conic = conic; p.opacity = opacity;
+    p.rgb = rgb;
+    for (int i = 0; i < 3; ++i) p.bg[i] = bg3 ? bg3[i] : 0.f;
+    p.alpha_max = opts->alpha_max;
+    p.early_cull = opts->early_cull;
+    p.img = img; p.T_final = T_final; p.n_contrib = n_contrib; p.dL_dimg = dL_dimg;
+    p.dmean2d = dmean2d; p.dconic = dconic; p.dopacity = dopacity; p.drgb = drgb;
+    int tiles = p.cam.grid_w * p.cam.grid_h;
+    k_render_bwd<<<tiles, kFwdThreads, 0, (cudaStream_t)stream>>>(p);
+    TCGS_CHECK_LAUNCH();
+    return TCGS_OK;
+}

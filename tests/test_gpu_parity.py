@@ -1,0 +1,304 @@
+"""GPU parity of every stage against the FP64 oracle, through the C ABI.
+
+Bars (stated per test): bit-exact for binning/sort (integer work); FP32 render max |RGB| <= 1e-5
+outside decision-margin pixels (counted, expected << 0.1%); TC render PSNR >= 50 dB and >= 99.9% of
+pixels within 2e-3; Frag2Mat exponents within the Appendix-A bound; backward within 1e-4 relative
+of the oracle's analytic gradient (itself pinned by finite differences)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import frag2mat as f2m
+from paper_2505_24796_gb300 import scenes
+
+from .helpers import f32, oracle_frame, psnr, scene64, to_torch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import paper_2505_24796_gb300 as m
+    m._lib.load()
+    return m
+
+
+def gpu_inputs(inp, b):
+    return dict(mean2d=to_torch(inp["mean2d"], DEV), conic=to_torch(inp["conic"], DEV),
+                depth=to_torch(inp["depth"], DEV), radius=to_torch(inp["radius"].astype(np.int32), DEV),
+                rgb=to_torch(inp["rgb"], DEV), opacity=to_torch(inp["opacity"], DEV),
+                ranges=to_torch(b["ranges"].astype(np.int32), DEV),
+                ids=to_torch(b["ids"].astype(np.int32) if b["n"] > 0 else np.zeros(1, np.int32), DEV))
+
+
+# workloads: (name, factory kwargs) -- small enough for the oracle, several tiles, ragged edges
+SMALL = [
+    ("plain_128", lambda: scenes.plain_forward()),
+    ("plain_ragged_200x136", lambda: scenes.plain_forward(P=1500, width=200, height=136, seed=11)),
+    ("precision_crop_240x120", lambda: scenes.precision(P=30_000, width=240, height=120, seed=12)),
+]
+
+
+# ------------------------------------------------------------------ projection
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_project_matches_oracle(tc, name, make):
+    cam, sc = make()
+    pr = oracle.project(cam, scene64(sc))
+    dsc = {k: to_torch(v, DEV) for k, v in sc.items() if isinstance(v, np.ndarray)}
+    out = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], sc["sh_degree"])
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    vis_o = pr["radius"] > 0
+    vis_g = g["radius"] > 0
+    # visibility may only differ where the decision is on a rounding edge (radius ceil or tile edge)
+    diff = vis_o != vis_g
+    assert diff.mean() < 1e-3, (name, diff.sum())
+    both = vis_o & vis_g
+    np.testing.assert_allclose(g["mean2d"][both], pr["mean2d"][both], rtol=2e-6, atol=2e-4)
+    np.testing.assert_allclose(g["depth"][both], pr["depth"][both], rtol=1e-6)
+    scale = np.abs(pr["conic"][both]).max(axis=1, keepdims=True)
+    cerr = np.abs(g["conic"][both] - pr["conic"][both]) / scale
+    print(f"\n[project] {name}: max rel conic err {cerr.max():.3g}, mean2d err "
+          f"{np.abs(g['mean2d'][both] - pr['mean2d'][both]).max():.3g}")
+    assert cerr.max() <= 1e-3
+    np.testing.assert_allclose(g["rgb"][both], pr["rgb"][both], atol=2e-6)
+    rad_diff = g["radius"][both] != pr["radius"][both]
+    assert rad_diff.mean() < 1e-3
+    assert (np.abs(g["radius"][both] - pr["radius"][both]) <= 1).all()
+
+
+# ------------------------------------------------------------------ binning (bit exact)
+
+@pytest.mark.parametrize("name,make", SMALL + [("diff_crop_320x180", lambda: scenes.differentiation(
+    P=20_000, width=320, height=180, seed=13)[:2])])
+def test_bin_sort_bit_exact(tc, name, make):
+    cam, sc = make()
+    pr = oracle.project(cam, scene64(sc))
+    inp = dict(mean2d=f32(pr["mean2d"]), radius=pr["radius"], depth=f32(pr["depth"]))
+    b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"])
+    m = to_torch(inp["mean2d"], DEV); r = to_torch(inp["radius"].astype(np.int32), DEV)
+    d = to_torch(inp["depth"], DEV)
+    out = tc.tcgs_bin_sort(cam, m, r, d, capacity=b["n"] + 17)
+    torch.cuda.synchronize()
+    assert int(out["status"].item()) == 0
+    assert int(out["n_splats"].item()) == b["n"]
+    np.testing.assert_array_equal(out["ids_sorted"].cpu().numpy()[: b["n"]], b["ids"])
+    np.testing.assert_array_equal(out["tile_ranges"].cpu().numpy(), b["ranges"])
+
+
+def test_bin_sort_capacity_overflow_reports_status(tc):
+    cam, sc = scenes.plain_forward()
+    pr = oracle.project(cam, scene64(sc))
+    n = int(pr["tiles_touched"].sum())
+    m = to_torch(f32(pr["mean2d"]), DEV); r = to_torch(pr["radius"].astype(np.int32), DEV)
+    d = to_torch(f32(pr["depth"]), DEV)
+    out = tc.tcgs_bin_sort(cam, m, r, d, capacity=n - 1)
+    torch.cuda.synchronize()
+    assert int(out["status"].item()) == 3 and int(out["n_splats"].item()) == n
+    assert (out["tile_ranges"][:, 0] == out["tile_ranges"][:, 1]).all()
+
+
+def test_bin_sort_empty_and_all_culled(tc):
+    cam = scenes.pinhole(40, 24, fx=40.0)
+    for P in [0, 5]:
+        m = torch.zeros(P, 2, device=DEV); r = torch.zeros(P, dtype=torch.int32, device=DEV)
+        d = torch.ones(P, device=DEV)
+        out = tc.tcgs_bin_sort(cam, m, r, d, capacity=8)
+        torch.cuda.synchronize()
+        assert int(out["n_splats"].item()) == 0 and int(out["status"].item()) == 0
+        assert (out["tile_ranges"] == 0).all()
+
+
+def test_bin_sort_depth_ties_and_huge_gaussian(tc):
+    cam = scenes.pinhole(100, 70, fx=100.0)
+    rng = np.random.default_rng(3)
+    P = 400
+    mean2d = f32(np.c_[rng.uniform(-30, 130, P), rng.uniform(-30, 100, P)])
+    radius = rng.integers(0, 40, P).astype(np.int32)
+    radius[7] = 100000         # covers every tile
+    mean2d[9] = [-1e9, 5.0]    # far off-screen
+    depth = f32(rng.choice([1.0, 2.0, 3.0], P))   # many exact ties
+    b = oracle.bin_sort(cam, mean2d, radius, depth)
+    out = tc.tcgs_bin_sort(cam, to_torch(mean2d, DEV), to_torch(radius, DEV), to_torch(depth, DEV), capacity=b["n"])
+    torch.cuda.synchronize()
+    assert int(out["n_splats"].item()) == b["n"]
+    np.testing.assert_array_equal(out["ids_sorted"].cpu().numpy()[: b["n"]], b["ids"])
+    np.testing.assert_array_equal(out["tile_ranges"].cpu().numpy(), b["ranges"])
+
+
+# ------------------------------------------------------------------ alpha blending
+
+def margin_mask(o, cull_tol, term_tol):
+    return (o["cull_margin"] < cull_tol) | (o["term_margin"] < term_tol)
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+@pytest.mark.parametrize("alpha_max,bg", [(0.99, (0, 0, 0)), (1.0, (0.25, 0.5, 0.75))])
+def test_render_fp32_matches_oracle(tc, name, make, alpha_max, bg):
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc, alpha_max=alpha_max, bg=bg)
+    g = gpu_inputs(inp, b)
+    stats = torch.zeros(b["ranges"].shape[0], 4, dtype=torch.int32, device=DEV)
+    out = tc.tcgs_render_fwd(cam, tc.render_opts("fp32", alpha_max, tile_stats=stats), g["ranges"], g["ids"],
+                             g["mean2d"], g["conic"], g["opacity"], g["rgb"], bg=bg)
+    torch.cuda.synchronize()
+    img, T, nc = (out[k].cpu().numpy() for k in ("img", "T_final", "n_contrib"))
+    excl = margin_mask(o, 1e-4, 1e-4)
+    assert excl.mean() < 1e-3
+    keep = ~excl
+    err = np.abs(img - o["img"]).max(axis=0)
+    assert err[keep].max() <= 1e-5, err[keep].max()
+    assert np.abs(T - o["T"])[keep].max() <= 1e-5
+    assert (nc[keep] == o["n_contrib"][keep]).all()
+    s = stats.cpu().numpy().astype(np.int64)
+    # fragment classes agree with the oracle's counts up to margin pixels
+    assert abs(s[:, 0].sum() - o["f_blend"]) <= max(10, 1e-4 * o["f_blend"])
+    assert abs(s[:, 0].sum() + s[:, 1].sum() - o["alpha_evals"]) <= max(10, 1e-3 * o["alpha_evals"])
+    np.testing.assert_array_equal(s[:, 3], b["ranges"][:, 1] - b["ranges"][:, 0])
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_render_fp32_early_cull_same_image(tc, name, make):
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    a = tc.tcgs_render_fwd(cam, tc.render_opts("fp32", early_cull=False), g["ranges"], g["ids"], g["mean2d"],
+                           g["conic"], g["opacity"], g["rgb"])["img"]
+    c = tc.tcgs_render_fwd(cam, tc.render_opts("fp32", early_cull=True), g["ranges"], g["ids"], g["mean2d"],
+                           g["conic"], g["opacity"], g["rgb"])["img"]
+    torch.cuda.synchronize()
+    diff = (a - c).abs().amax(dim=0).cpu().numpy()
+    assert (diff > 1e-6).mean() < 1e-3   # only cull-margin fragments can differ
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+@pytest.mark.parametrize("alpha_max", [0.99, 1.0])
+def test_render_tc_split_matches_oracle(tc, name, make, alpha_max):
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc, alpha_max=alpha_max)
+    g = gpu_inputs(inp, b)
+    stats = torch.zeros(b["ranges"].shape[0], 4, dtype=torch.int32, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    out = tc.tcgs_render_fwd(cam, tc.render_opts("tc_fp16_split", alpha_max, tile_stats=stats, device_status=status),
+                             g["ranges"], g["ids"], g["mean2d"], g["conic"], g["opacity"], g["rgb"])
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    img = out["img"].cpu().numpy()
+    err = np.abs(img - o["img"]).max(axis=0)
+    p = psnr(img, o["img"])
+    within = (err <= 2e-3).mean()
+    assert p >= 50.0, p
+    assert within >= 0.999, within
+    s = stats.cpu().numpy().astype(np.int64)
+    assert abs(s[:, 0].sum() - o["f_blend"]) <= max(20, 1e-3 * o["f_blend"])
+    np.testing.assert_array_equal(s[:, 3], b["ranges"][:, 1] - b["ranges"][:, 0])
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_render_tc_paper_padding_reports_error(tc, name, make):
+    """The paper's K = 8 layout (v0 / 3 three times): accuracy is reported, with a loose floor."""
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    out = tc.tcgs_render_fwd(cam, tc.render_opts("tc_fp16"), g["ranges"], g["ids"], g["mean2d"], g["conic"],
+                             g["opacity"], g["rgb"])
+    torch.cuda.synchronize()
+    img = out["img"].cpu().numpy()
+    p = psnr(img, o["img"])
+    print(f"\n[tc_fp16 paper padding] {name}: PSNR {p:.2f} dB, within 2e-3: "
+          f"{(np.abs(img - o['img']).max(axis=0) <= 2e-3).mean():.5f}")
+    assert p >= 30.0
+
+
+def test_render_outputs_empty_tiles_background(tc):
+    cam = scenes.pinhole(33, 17, fx=33.0)
+    nt = 3 * 2
+    ranges = torch.zeros(nt, 2, dtype=torch.int32, device=DEV)
+    ids = torch.zeros(1, dtype=torch.int32, device=DEV)
+    z = torch.zeros(1, 2, device=DEV)
+    for prec in ["fp32", "tc_fp16_split", "tc_fp16"]:
+        out = tc.tcgs_render_fwd(cam, tc.render_opts(prec), ranges, ids, z, torch.zeros(1, 3, device=DEV),
+                                 torch.ones(1, device=DEV), torch.zeros(1, 3, device=DEV), bg=(0.1, 0.2, 0.3))
+        torch.cuda.synchronize()
+        img = out["img"].cpu().numpy()
+        np.testing.assert_allclose(img[:, 0, 0], [0.1, 0.2, 0.3], rtol=1e-6)
+        assert (out["T_final"] == 1).all() and (out["n_contrib"] == 0).all()
+
+
+# ------------------------------------------------------------------ Frag2Mat error bound (Appendix A)
+
+@pytest.mark.parametrize("precision,factor", [("tc_fp16", 1.0), ("tc_fp16_split", 2.0 ** -10)])
+def test_frag2mat_exponents_within_appendix_bound(tc, precision, factor):
+    cam, sc = scenes.precision(P=30_000, width=240, height=120, seed=12)
+    _, inp, b, _ = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    gw, gh = oracle.grid(cam)
+    lens = b["ranges"][:, 1] - b["ranges"][:, 0]
+    tiles = np.nonzero(lens > 0)[0][:24]
+    max_n = int(lens[tiles].max())
+    beta = tc.tcgs_frag2mat_beta(cam, precision, g["ranges"], g["ids"], g["mean2d"], g["conic"], g["opacity"],
+                                 tiles, max_n).cpu().numpy()
+    checked = 0
+    for k, t in enumerate(tiles):
+        s, e = b["ranges"][t]
+        ids = b["ids"][s:e]
+        _, _, bex, absum = f2m.local_products(t % gw, t // gw, inp["mean2d"][ids], inp["conic"][ids],
+                                              inp["opacity"][ids])
+        keep = bex >= -math.log(255.0)
+        bh = beta[k, :, : e - s]
+        # paper bound (2 eps_H sum|u_i v_i|) scaled for the split layout, plus FP32 v-construction
+        # and accumulation slack (v is built from FP32 inputs in FP32)
+        bound = factor * f2m.paper_bound(absum) + 8 * 2.0 ** -24 * (absum + 8 * np.abs(bex)) + 1e-6
+        err = np.abs(bh - bex)
+        assert (err[keep] <= bound[keep]).all(), (precision, t, float((err - bound)[keep].max()))
+        checked += int(keep.sum())
+    assert checked > 1000
+
+
+# ------------------------------------------------------------------ backward
+
+@pytest.mark.parametrize("name,make", SMALL[:2])
+def test_backward_matches_oracle_gradient(tc, name, make):
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    rng = np.random.default_rng(21)
+    gimg = f32(rng.standard_normal((3, cam["height"], cam["width"])))
+    ref = oracle.render_bwd(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["rgb"], gimg)
+    fwd = tc.tcgs_render_fwd(cam, tc.render_opts("fp32"), g["ranges"], g["ids"], g["mean2d"], g["conic"],
+                             g["opacity"], g["rgb"])
+    grads = tc.tcgs_render_bwd(cam, tc.render_opts("fp32"), g["ranges"], g["ids"], g["mean2d"], g["conic"],
+                               g["opacity"], g["rgb"], fwd["img"], fwd["T_final"], fwd["n_contrib"],
+                               to_torch(gimg, DEV))
+    torch.cuda.synchronize()
+    # Gaussians touching a decision-margin pixel may legitimately differ
+    excl = margin_mask(o, 1e-4, 1e-4)
+    for key, rk in [("dmean2d", "dmean2d"), ("dconic", "dconic"), ("dopacity", "dopacity"), ("drgb", "drgb")]:
+        a = grads[key].cpu().numpy().reshape(len(inp["opacity"]), -1)
+        r = ref[rk].reshape(len(inp["opacity"]), -1)
+        scale = np.abs(r).max(axis=1, keepdims=True) + 1e-3 * np.abs(r).max()
+        rel = np.abs(a - r) / scale
+        bad = (rel > 1e-4).any(axis=1)
+        assert bad.mean() <= max(excl.mean() * 50, 2e-3), (key, bad.sum(), float(rel.max()))
+
+
+def test_autograd_function_matches_backward(tc):
+    cam, sc = scenes.plain_forward(P=300, width=64, height=64, seed=31)
+    _, inp, b, o = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    params = [g[k].clone().requires_grad_(True) for k in ("mean2d", "conic", "opacity", "rgb")]
+    target = torch.rand(3, 64, 64, device=DEV, generator=torch.Generator(DEV).manual_seed(0))
+    img, T = tc.rasterize(*params, cam, g["ranges"], g["ids"], precision="fp32")
+    loss = (img - target).abs().sum()
+    loss.backward()
+    gimg = torch.sign(img.detach() - target).cpu().numpy().astype(np.float32)
+    ref = oracle.render_bwd(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["rgb"], gimg)
+    for p, k in zip(params, ("dmean2d", "dconic", "dopacity", "drgb")):
+        a = p.grad.cpu().numpy().reshape(ref[k].shape)
+        np.testing.assert_allclose(a, ref[k], rtol=1e-3, atol=1e-4 * np.abs(ref[k]).max())
