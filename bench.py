@@ -1,0 +1,396 @@
+"""Benchmark of the TC-GS rasterizer hot path on one GB300 (or N replicas under torchrun).
+
+One step = one frame of the precision workload (1920x1080, fx = fy = 1100, 1M Gaussians in
+64 clusters, SH degree 3): project -> bin_sort -> render_fwd with the Frag2Mat tensor-core
+path (FP16 hi/lo split, G2L).  Inputs are resident in HBM; L2 is flushed between steps
+(outside the timed events).  The same frame on the FP32 CUDA-core path is timed beside it.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
+bounded sample of the same workload per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tcgs|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & alpha-evals/s, TC-FP16 vs FP32 path, 1 GB300, PSNR>=50dB vs FP64 oracle"
+WORKLOAD = ("precision: 1 view 1920x1080, fx=fy=1100, 1M Gaussians from a 64-cluster anisotropic mixture, "
+            "z in [1,50], log-scales N(-4.5,1), bimodal opacity, SH degree 3, seed 2")
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+SM_COUNT, SM_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tcgs", choices=["tcgs", "reference"])
+    ap.add_argument("--precision", default="tc_fp16_split", choices=["tc_fp16_split", "tc_fp16"])
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels eagerly instead of a CUDA graph")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 1M Gaussians (profiling runs)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def workload(scale=1.0):
+    from paper_2505_24796_gb300 import scenes
+    return scenes.precision(P=int(round(1_000_000 * scale)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_frame_estimate(cam, sc, tile_fraction, seed=0):
+    """Time the FP64 oracle on one bounded sample of a frame: projection and binning of the whole
+    scene, Algorithm 1 on a random subset of tiles; returns (seconds per full frame, sample info)."""
+    import oracle
+    s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    t0 = time.perf_counter()
+    pr = oracle.project(cam, s64)
+    t1 = time.perf_counter()
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    t2 = time.perf_counter()
+    gw, gh = oracle.grid(cam)
+    nt = gw * gh
+    k = max(1, int(round(nt * tile_fraction)))
+    tiles = np.random.default_rng(seed).choice(nt, k, replace=False)
+    o = oracle.render(cam, b, pr["mean2d"], pr["conic"], s64["opacity"], pr["rgb"], tiles=tiles, margins=False)
+    t3 = time.perf_counter()
+    est = (t1 - t0) + (t2 - t1) + (t3 - t2) * nt / k
+    info = dict(project_s=t1 - t0, bin_s=t2 - t1, render_sample_s=t3 - t2, tiles_sampled=k, tiles=nt,
+                cpu_work_s=t3 - t0, frame_s_est=est, img=o["img"], tiles_list=tiles)
+    return est, info
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, single-threaded on the host."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cam, sc = workload(args.scale)
+    frac = 1.0 / 64
+    times = []
+    for i in range(args.warmup + args.steps):
+        est, info = oracle_frame_estimate(cam, sc, frac, seed=i)
+        if i >= args.warmup:
+            times.append(est)
+    t = statistics.mean(times)
+    v = 1.0 / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "P": len(sc["opacity"])},
+        "cpu_baseline": {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: FP64 projection + binning of the whole scene, Algorithm 1 on "
+                                   f"{frac:.4f} of the tiles (random, seeded per step), extrapolated to the frame"},
+        "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_tcgs(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2505_24796_gb300 as tc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = tc._lib.load()
+
+    cam, sc = workload(args.scale)
+    P = len(sc["opacity"])
+    dsc = tc.scene_to_device(sc, dev)
+    H, W = cam["height"], cam["width"]
+
+    # --- setup (untimed): splat count and capacity, fragment classes from the FP32 counters
+    probe = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], dsc["sh_degree"])
+    n_splats = int(probe["tiles_touched"].to(torch.int64).sum().item())
+    capacity = n_splats + 1024
+    r = tc.Renderer(cam, P, capacity, device=dev, stats=True)
+    r.frame(dsc, precision="fp32")
+    torch.cuda.synchronize()
+    st = r.stats.to(torch.int64).sum(dim=0).tolist()
+    f_blend, f_cull, slots_fp32 = st[0], st[1], st[2]
+    alpha_evals = f_blend + f_cull
+    img_fp32 = r.out["img"].clone()
+    r.stats.zero_()
+    r.frame(dsc, precision=args.precision)
+    torch.cuda.synchronize()
+    st_tc = r.stats.to(torch.int64).sum(dim=0).tolist()
+    img_tc = r.out["img"].clone()
+    status = (int(r.bins["status"].item()), int(r.device_status.item()))
+    r.stats = None  # no counters in the timed region
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (126 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def stage_fns(precision):
+        return [lambda: r.project(dsc), lambda: r.bin_sort(), lambda: r.render(dsc["opacity"], precision)]
+
+    def time_frames(precision, steps, warmup, use_graph):
+        fns = stage_fns(precision)
+        graphs = None
+        if use_graph:
+            # one CUDA graph per stage so each stage keeps its own events
+            for f in fns:
+                f()
+            torch.cuda.synchronize()
+            graphs = []
+            for f in fns:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    f()
+                graphs.append(g)
+            run = [g.replay for g in graphs]
+        else:
+            run = fns
+        for _ in range(warmup):
+            for f in run:
+                f()
+        torch.cuda.synchronize()
+        per_stage = [[] for _ in run]
+        total = []
+        for _ in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(run) + 1)]
+            ev[0].record(stream)
+            for i, f in enumerate(run):
+                f()
+                ev[i + 1].record(stream)
+            ev[-1].synchronize()
+            for i in range(len(run)):
+                per_stage[i].append(ev[i].elapsed_time(ev[i + 1]))
+            total.append(ev[0].elapsed_time(ev[-1]))
+        return total, per_stage
+
+    use_graph = not args.no_graph
+    # --- FP32 comparison path
+    tot32, st32 = time_frames("fp32", args.steps, args.warmup, use_graph)
+    # --- headline path, with clocks sampled during the timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = lib.tcgs_kernel_launches()
+    with ClockSampler(local) as clk:
+        tot, stg = time_frames(args.precision, args.steps, args.warmup, use_graph)
+    launches_total = lib.tcgs_kernel_launches() - l0
+    torch.cuda.synchronize()
+    # launches per frame, counted by the library on one eager frame (graphs replay the same kernels)
+    l1 = lib.tcgs_kernel_launches()
+    r.frame(dsc, precision=args.precision)
+    torch.cuda.synchronize()
+    launches_per_frame = lib.tcgs_kernel_launches() - l1
+    ms = statistics.mean(tot)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    fps = world * 1000.0 / ms
+    ms32 = statistics.mean(tot32)
+    render_ms = statistics.mean(stg[2])
+    render32_ms = statistics.mean(st32[2])
+
+    # --- end to end through the public API with host buffers: H2D of the scene, D2H of the image
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in sc.items()
+              if isinstance(v, np.ndarray)}
+    host_img = torch.empty(3, H, W, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in pinned.values())
+    d2h = host_img.numel() * 4
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k, v in pinned.items():
+            dsc[k].copy_(v, non_blocking=True)
+        out = r.frame(dsc, precision=args.precision)
+        host_img.copy_(out["img"], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_fps = world * 1000.0 / statistics.mean(e2e_ms)
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # --- accuracy of this frame: TC vs FP32 on the GPU, and vs the FP64 oracle on the sampled tiles
+    img_tc_np = img_tc.cpu().numpy().astype(np.float64)
+    img32_np = img_fp32.cpu().numpy().astype(np.float64)
+    mse_tc_fp32 = float(np.mean((img_tc_np - img32_np) ** 2))
+    cpu_baseline = None
+    acc = {"psnr_tc_vs_fp32_db": (10 * math.log10(1 / mse_tc_fp32) if mse_tc_fp32 > 0 else None)}
+    if not args.no_cpu_baseline:
+        est, info = oracle_frame_estimate(cam, sc, 0.5, seed=1)
+        cpu_baseline = {"value": 1.0 / est, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                        "sample": f"FP64 projection + binning of the whole scene, Algorithm 1 on "
+                                  f"{info['tiles_sampled']}/{info['tiles']} random tiles, extrapolated; "
+                                  f"{info['cpu_work_s']:.1f} s of CPU work"}
+        gw = (W + 15) // 16
+        mask = np.zeros((H, W), bool)
+        for t in info["tiles_list"]:
+            ty, tx = divmod(int(t), gw)
+            mask[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
+        oimg = info["img"]
+        for name, im in (("tc", img_tc_np), ("fp32", img32_np)):
+            d = (im - oimg)[:, mask]
+            mse = float(np.mean(d ** 2))
+            acc[f"psnr_{name}_vs_oracle_db"] = 10 * math.log10(1 / mse) if mse > 0 else None
+            acc[f"within_2e-3_{name}"] = float((np.abs(d).max(axis=0) <= 2e-3).mean())
+            acc[f"max_abs_{name}"] = float(np.abs(d).max())
+        acc["oracle_pixels_compared"] = int(mask.sum())
+
+    # --- roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    stage_names = ["project", "bin_sort", "render_fwd"]
+    stage_ms = [statistics.mean(s) for s in stg]
+    dominant = stage_names[int(np.argmax(stage_ms))]
+    ops = alpha_evals * 1 + f_blend * 8   # EarlyCull compare per evaluated fragment + 8 FP32 ops per blend
+    alu_peak = SM_COUNT * SM_LANES * SM_MAX_MHZ * 1e6 / 1e12   # thread-ops/s at max clock, TOP/s
+    rl_render = {"bound": "alu", "achieved": ops / (render_ms * 1e-3) / 1e12, "peak": alu_peak, "unit": "TOP/s",
+                 "traffic": None, "kernel": "k_render_tc",
+                 "tensor_tflops": 12 * alpha_evals / (render_ms * 1e-3) / 1e12,
+                 "tensor_peak_tflops": peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")),
+                 "peak_source": f"alu: {SM_COUNT} SMs x {SM_LANES} lanes x {SM_MAX_MHZ:.0f} MHz; tensor: {peak_src}"}
+    rl_render["frac"] = rl_render["achieved"] / rl_render["peak"]
+    rl_render["tensor_frac"] = rl_render["tensor_tflops"] / rl_render["tensor_peak_tflops"]
+    tile_bits = max(1, math.ceil(math.log2(r.num_tiles)))
+    tpasses = 1 if tile_bits <= 8 else (2 if tile_bits <= 16 else 3)
+    bin_bytes = P * (4 * 20 + 8 + 24) + n_splats * (8 + tpasses * 20 + 8)
+    rl_bin = {"bound": "hbm", "achieved": bin_bytes / (stage_ms[1] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+              "unit": "GB/s", "traffic": None, "kernel": "tcgs_bin_sort (whole stage)",
+              "peak_source": peak_src}
+    rl_bin["frac"] = rl_bin["achieved"] / rl_bin["peak"]
+    proj_bytes = P * (12 + 12 + 16 + 192 + 44)
+    rl_proj = {"bound": "hbm", "achieved": proj_bytes / (stage_ms[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+               "unit": "GB/s", "traffic": None, "kernel": "k_project", "peak_source": peak_src}
+    rl_proj["frac"] = rl_proj["achieved"] / rl_proj["peak"]
+    roof = {"project": rl_proj, "bin_sort": rl_bin, "render_fwd": rl_render}[dominant]
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16 tensor-core exponent, f32 accumulate and blend", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "P": P, "splats": n_splats, "precision": args.precision,
+                   "l2": "flushed (256 MB write) between timed steps, outside the events",
+                   "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "single GPU"},
+        "alpha_evals_per_frame": alpha_evals, "f_blend": f_blend, "f_cull": f_cull,
+        "alpha_evals_per_s": alpha_evals / (render_ms * 1e-3),
+        "stages_ms": dict(zip(stage_names, stage_ms)),
+        "fp32": {"frames_per_s": 1000.0 / ms32, "ms_per_step": ms32,
+                 "stages_ms": dict(zip(stage_names, [statistics.mean(s) for s in st32])),
+                 "alpha_evals_per_s": alpha_evals / (render32_ms * 1e-3)},
+        "speedup_vs_fp32": {"frame": ms32 / ms * world / world, "render": render32_ms / render_ms},
+        "accuracy": acc, "status": {"bin_sort": status[0], "render": status[1]},
+        "executed_fragment_slots": {"fp32": slots_fp32, "tc": st_tc[2]},
+        "roofline": roof, "roofline_all": {"project": rl_proj, "bin_sort": rl_bin, "render_fwd": rl_render},
+        "cpu_baseline": cpu_baseline,
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches_per_frame * args.steps), "gpu_launches_per_frame": int(launches_per_frame),
+        "gpu_launches_counted_in_capture": int(launches_total),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_tcgs(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,10 @@ TCGS_API const char* tcgs_status_string(int status);
 /* Library version, 100 * major + minor. */
 TCGS_API int tcgs_version(void);
 
+/* Number of CUDA kernels this library has launched in this process so far (a host-side counter,
+ * incremented once per kernel launch; no device work, no synchronisation). */
+TCGS_API uint64_t tcgs_kernel_launches(void);
+
 /*
  * Preprocess (Sec. 3.1, Eq. 2): EWA projection of P 3D Gaussians.
  *   Sigma = R(q) diag(s)^2 R(q)^T, t = W mu, J = d(mean2d)/d(t) at t with x/z, y/z

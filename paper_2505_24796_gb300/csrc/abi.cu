@@ -1,5 +1,12 @@
 // abi.cu -- status strings and version of the C ABI (include/tcgs.h).
+#include <atomic>
+
 #include "common.cuh"
+
+namespace tcgs {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace tcgs
 
 extern "C" const char* tcgs_status_string(int status) {
     switch (status) {
@@ -14,3 +21,5 @@ extern "C" const char* tcgs_status_string(int status) {
 }
 
 extern "C" int tcgs_version(void) { return 100; }
+
+extern "C" uint64_t tcgs_kernel_launches(void) { return tcgs::g_launches.load(std::memory_order_relaxed); }

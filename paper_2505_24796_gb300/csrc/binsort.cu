@@ -329,8 +329,11 @@ inline void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
     uint32_t* tot = w.digit_total + (pass & 1) * kRadix;
     uint32_t* nxt = w.digit_total + ((pass + 1) & 1) * kRadix;
     k_radix_hist<<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, G, w.hist, tot);
+    count_launches(1);
     k_radix_scan<<<kRadix, kThreads, 0, s>>>(w.hist, tot, nxt, G);
+    count_launches(1);
     k_radix_scatter<<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, G, w.hist);
+    count_launches(1);
 }
 
 }  // namespace
@@ -366,6 +369,7 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     k_bin_keys<<<(n_init + kThreads - 1) / kThreads, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, w.dk_a, w.dv_a,
                                                                        w.counts, tile_ranges, 2 * num_tiles,
                                                                        w.digit_total);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 1. depth order (4 passes; the result returns to the a-buffers)
     int pass = 0;
@@ -383,10 +387,13 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     int G2 = P < kScanBlocks * 256 ? (P + 255) / 256 : kScanBlocks;
     if (G2 < 1) G2 = 1;
     if (P > 0) k_scan_reduce<<<G2, kThreads, 0, s>>>(w.counts, order, (uint32_t)P, G2, w.block_sums);
+    if (P > 0) count_launches(1);
     else cudaMemsetAsync(w.block_sums, 0, 8, s);
     k_scan_top<<<1, 1024, 0, s>>>(w.block_sums, G2, splat_capacity, n_splats, status, w.n_u32);
+    count_launches(1);
     if (P > 0)
         k_scan_final<<<G2, kThreads, 0, s>>>(w.counts, order, (uint32_t)P, G2, w.block_sums, w.offsets, w.n_u32);
+        count_launches(1);
     TCGS_CHECK_LAUNCH();
     if (splat_capacity == 0 || P == 0) return TCGS_OK;
     // 3. duplication into the buffer the first tile pass reads
@@ -398,6 +405,7 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     int src = (tpasses & 1) ? 1 : 0;
     k_duplicate<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts,
                                                                   mean2d, radius, kbuf[src], vbuf[src], w.n_u32);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 4. stable sort by tile id
     int Gs = sort_blocks(splat_capacity);
@@ -409,6 +417,7 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     // 5. ranges
     int Gr = sort_blocks(splat_capacity) * 4;
     k_ranges<<<Gr, kThreads, 0, s>>>(kbuf[src], w.n_u32, tile_ranges);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }

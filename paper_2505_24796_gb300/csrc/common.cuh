@@ -89,6 +89,11 @@ __device__ __forceinline__ void set_status(int32_t* st, int code) {
 
 }  // namespace tcgs
 
+namespace tcgs {
+// host-side count of kernel launches (tcgs_kernel_launches)
+void count_launches(unsigned n);
+}
+
 #define TCGS_CHECK_LAUNCH()                                  \
     do {                                                     \
         cudaError_t e_ = cudaGetLastError();                 \

@@ -167,6 +167,7 @@ extern "C" tcgs_status tcgs_project(const tcgs_camera* cam, int32_t P, int32_t s
     int blocks = (P + threads - 1) / threads;
     k_project<<<blocks, threads, 0, (cudaStream_t)stream>>>(dc, P, sh_degree, means3, scales, quats, sh, mean2d,
                                                            conic, depth, radius, rgb, tiles_touched);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }

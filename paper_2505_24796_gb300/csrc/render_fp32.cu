@@ -259,6 +259,7 @@ tcgs_status launch_render_fp32(const tcgs_camera* cam, const tcgs_render_opts* o
     p.img = img; p.T_final = T_final; p.n_contrib = n_contrib; p.stats = opts->tile_stats;
     int tiles = p.cam.grid_w * p.cam.grid_h;
     k_render_fp32<<<tiles, kFwdThreads, 0, s>>>(p);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }
@@ -288,6 +289,7 @@ extern "C" tcgs_status tcgs_render_bwd(const tcgs_camera* cam, const tcgs_render
     p.dmean2d = dmean2d; p.dconic = dconic; p.dopacity = dopacity; p.drgb = drgb;
     int tiles = p.cam.grid_w * p.cam.grid_h;
     k_render_bwd<<<tiles, kFwdThreads, 0, (cudaStream_t)stream>>>(p);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }

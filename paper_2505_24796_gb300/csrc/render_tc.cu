@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
                 float2 m = reinterpret_cast<const float2*>(p.mean2d)[g];
                 float s11 = p.conic[3 * g], s12 = p.conic[3 * g + 1], s22 = p.conic[3 * g + 2];
                 float o = p.opacity[g];
-                col = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], 0.f);
+                if (!kInspect) col = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], 0.f);
                 float mx = m.x - cx, my = m.y - cy;   // G2L mean
                 float qx = s11 * mx + s12 * my, qy = s12 * mx + s22 * my;
                 float q0 = mx * qx + my * qy;
@@ -376,6 +376,7 @@ tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
         g_attr_set[kInspect] = true;
     }
     k_render_tc<kInspect><<<blocks, kTcThreads, kSmemDyn, s>>>(p);
+    count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }
