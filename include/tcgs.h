@@ -50,7 +50,8 @@ typedef enum {
     TCGS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
     TCGS_ERR_CAPACITY = 3,    /* more splats than the caller's capacity (device status word) */
     TCGS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (device status word) */
-    TCGS_ERR_UNSUPPORTED = 5  /* the current device cannot run this call (not sm_103a) */
+    TCGS_ERR_UNSUPPORTED = 5, /* the current device cannot run this call (not sm_103a) */
+    TCGS_ERR_SCRATCH_LIMIT = 6 /* the request needs more scratch than the built-in array holds */
 } tcgs_status;
 
 /* How the exponent beta = ln(o) - 1/2 d^T Sigma'^-1 d of Eq. (9) is evaluated. */
@@ -138,6 +139,35 @@ TCGS_API tcgs_status tcgs_bin_sort(const tcgs_camera* cam /* host */, int32_t P,
                           const int32_t* radius, const float* depth, int64_t splat_capacity,
                           void* workspace, size_t ws_bytes, uint32_t* ids_sorted, uint32_t* tile_ranges,
                           int64_t* n_splats, int32_t* status, tcgs_stream stream);
+
+/* Size of the scratch array built into the library for tcgs_bin_sort_noalloc (64 MiB). */
+#define TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/*
+ * tcgs_bin_sort for callers that cannot allocate device memory.  The paper has no counterpart.
+ * Some callers have no way to obtain a scratch buffer: code that runs while another component owns
+ * every allocation (a host application's memory manager, a framework allocator that only hands
+ * out its own tensors), code on a real-time or latency-critical path where cudaMalloc would
+ * synchronise the device, or thin C callers with no CUDA memory management of their own.  They
+ * still pass the inputs and outputs exactly as for tcgs_bin_sort; only `workspace` is replaced by
+ * a static device array of TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES inside libtcgs.so, which every GPU
+ * that loads the library holds until the process exits.
+ *   - Requests whose tcgs_bin_sort_workspace_size(P, splat_capacity, num_tiles) exceeds the array
+ *     return TCGS_ERR_SCRATCH_LIMIT at once (nothing enqueued).  64 MiB holds, for example,
+ *     P = 1,000 Gaussians with 5.4 million splats, or P = 500,000 with 4.5 million.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
+ *     that device current) and caches it; make that first call before any stream capture.
+ *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *   - All calls share the one array and it keeps whatever the previous call left there; the
+ *     kernels initialise every scratch word they read, so no clearing is needed between calls.
+ *     Calls that overlap on the GPU (two streams, or two host threads) race on the array and
+ *     produce garbage: serialise them.
+ * Arguments, outputs and device status as tcgs_bin_sort.
+ */
+TCGS_API tcgs_status tcgs_bin_sort_noalloc(const tcgs_camera* cam /* host */, int32_t P, const float* mean2d,
+                                           const int32_t* radius, const float* depth, int64_t splat_capacity,
+                                           uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_splats,
+                                           int32_t* status, tcgs_stream stream);
 
 /*
  * Conditional alpha-blending (Algorithm 1), front to back per pixel over its tile's list:

@@ -23,7 +23,7 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS
 
 TILE = 16
 
-__all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_render_fwd", "tcgs_render_bwd",
+__all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc", "tcgs_render_fwd", "tcgs_render_bwd",
            "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "TcgsError", "PRECISIONS",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8"]
 
@@ -124,6 +124,26 @@ def tcgs_bin_sort(cam, mean2d, radius, depth, capacity: int, workspace=None, out
         ctypes.byref(c), P, _ptr(mean2d, torch.float32, "mean2d"), _ptr(radius, torch.int32, "radius"),
         _ptr(depth, torch.float32, "depth"), int(capacity), _ptr(workspace, None, "workspace"),
         workspace.numel() * workspace.element_size(), _ptr(out["ids_sorted"], torch.int32),
+        _ptr(out["tile_ranges"], torch.int32), _ptr(out["n_splats"], torch.int64), _ptr(out["status"], torch.int32),
+        _stream(stream)))
+    return out
+
+
+def tcgs_bin_sort_noalloc(cam, mean2d, radius, depth, capacity: int, out=None, stream=None) -> dict:
+    """tcgs_bin_sort working in the library's built-in scratch array instead of a workspace
+    (for callers that cannot allocate device memory; see include/tcgs.h for the size limit and
+    the rule that calls must not overlap on the GPU)."""
+    c = _cam(cam)
+    dev = mean2d.device
+    nt = grid(c)[0] * grid(c)[1]
+    if out is None:
+        out = dict(ids_sorted=torch.empty(max(int(capacity), 1), dtype=torch.int32, device=dev),
+                   tile_ranges=torch.empty(nt, 2, dtype=torch.int32, device=dev),
+                   n_splats=torch.empty(1, dtype=torch.int64, device=dev),
+                   status=torch.empty(1, dtype=torch.int32, device=dev))
+    check("tcgs_bin_sort_noalloc", _L().tcgs_bin_sort_noalloc(
+        ctypes.byref(c), mean2d.shape[0], _ptr(mean2d, torch.float32, "mean2d"), _ptr(radius, torch.int32, "radius"),
+        _ptr(depth, torch.float32, "depth"), int(capacity), _ptr(out["ids_sorted"], torch.int32),
         _ptr(out["tile_ranges"], torch.int32), _ptr(out["n_splats"], torch.int64), _ptr(out["status"], torch.int32),
         _stream(stream)))
     return out

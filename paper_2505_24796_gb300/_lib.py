@@ -15,6 +15,8 @@ c_int32, c_int64, c_float, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64,
                                                  ctypes.c_size_t)
 
 TCGS_OK, TCGS_ERR_INVALID, TCGS_ERR_CUDA, TCGS_ERR_CAPACITY, TCGS_ERR_TIMEOUT, TCGS_ERR_UNSUPPORTED = range(6)
+TCGS_ERR_SCRATCH_LIMIT = 6
+TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS_TC_FP8 = range(4)
 PRECISIONS = {"fp32": TCGS_FP32, "tc_fp16": TCGS_TC_FP16, "tc_fp16_split": TCGS_TC_FP16_SPLIT, "tc_fp8": TCGS_TC_FP8}
 
@@ -41,6 +43,7 @@ SIGNATURES = {
     "tcgs_project": (c_int32, [P_CAM, c_int32, c_int32, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_bin_sort_workspace_size": (c_size_t, [c_int32, c_int64, c_int32]),
     "tcgs_bin_sort": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
+    "tcgs_bin_sort_noalloc": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, V, V, V, V]),
     "tcgs_render_fwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_render_bwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_frag2mat_beta": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int32, V, c_int32, V, V, V]),

@@ -16,6 +16,7 @@ extern "C" const char* tcgs_status_string(int status) {
         case TCGS_ERR_CAPACITY: return "splat capacity exceeded";
         case TCGS_ERR_TIMEOUT: return "device wait timed out";
         case TCGS_ERR_UNSUPPORTED: return "unsupported device (needs sm_103a)";
+        case TCGS_ERR_SCRATCH_LIMIT: return "request exceeds the built-in scratch array";
         default: return "unknown status";
     }
 }

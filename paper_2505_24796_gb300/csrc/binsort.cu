@@ -15,6 +15,8 @@
 // digit turns the counts into global output offsets.  scatter: each warp ranks its 32-key
 // rounds with __match_any_sync, warps and tiles are chained in order, so the pass is stable.
 // No block ever waits on another block.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace tcgs {
@@ -420,4 +422,43 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// The scratch array every tcgs_bin_sort_noalloc call works in.  Host code must not pass its name
+// to a kernel (on the host it is only a stand-in symbol): the device address is looked up once
+// per device with cudaGetSymbolAddress and passed on as an ordinary workspace pointer.
+static __device__ __align__(256) unsigned char g_bin_sort_scratch[TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxNoallocDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxNoallocDevices] = {};
+}  // namespace
+
+extern "C" tcgs_status tcgs_bin_sort_noalloc(const tcgs_camera* cam, int32_t P, const float* mean2d,
+                                             const int32_t* radius, const float* depth, int64_t splat_capacity,
+                                             uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_splats,
+                                             int32_t* status, tcgs_stream stream) {
+    if (!tcgs::valid_camera(cam) || P < 0 || splat_capacity < 0 || splat_capacity > (int64_t)0xFFFFFFFFu)
+        return TCGS_ERR_INVALID;
+    const tcgs::DevCamera dc = tcgs::make_dev_camera(*cam);
+    const size_t need = tcgs_bin_sort_workspace_size(P, splat_capacity, dc.grid_w * dc.grid_h);
+    if (need > (size_t)TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES) return TCGS_ERR_SCRATCH_LIMIT;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxNoallocDevices) return TCGS_ERR_CUDA;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_bin_sort_scratch) != cudaSuccess || !p) return TCGS_ERR_CUDA;
+            g_scratch_addr[dev] = p;
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    return tcgs_bin_sort(cam, P, mean2d, radius, depth, splat_capacity, scratch,
+                         (size_t)TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES, ids_sorted, tile_ranges, n_splats, status,
+                         stream);
 }
