@@ -78,6 +78,9 @@ typedef struct {
     int32_t precision;       /* tcgs_precision */
     float alpha_max;         /* alpha clamp (0.99 as in the official 3DGS renderer; 1 = Algorithm 1 literally) */
     int32_t early_cull;      /* FP32 path only: test beta < -ln 255 before exp (Sec. 4.1); TC paths always do */
+    int32_t tile_cull;       /* TC paths: 1 = skip, per 8x4 pixel block, list entries whose Gaussian cannot
+                                reach alpha >= 1/255 at any pixel of the block (exact minimum of the conic
+                                form over the block; the image is unchanged); 0 = walk every entry */
     uint32_t* tile_stats;    /* nullable device [num_tiles * 4], accumulated (+=) per tile:
                                 [0] blended fragments, [1] evaluated but not blended fragments
                                 (culled, plus the fragment that triggers termination),

@@ -73,11 +73,12 @@ def _cam(cam) -> tcgs_camera:
 
 
 def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=False, tile_stats=None,
-                device_status=None) -> tcgs_render_opts:
+                device_status=None, tile_cull=True) -> tcgs_render_opts:
     o = tcgs_render_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.alpha_max = float(alpha_max)
     o.early_cull = int(bool(early_cull))
+    o.tile_cull = int(bool(tile_cull))
     o.tile_stats = _ptr(tile_stats, torch.int32, "tile_stats") if tile_stats is not None else None
     o.device_status = _ptr(device_status, torch.int32, "device_status") if device_status is not None else None
     return o
@@ -249,8 +250,8 @@ class Renderer:
                              workspace=self.ws, out=self.bins, stream=stream)
 
     def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=False, bg=(0, 0, 0),
-               stream=None):
-        opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status)
+               stream=None, tile_cull=True):
+        opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status, tile_cull)
         return tcgs_render_fwd(self.cam, opts, self.bins["tile_ranges"], self.bins["ids_sorted"],
                                self.proj["mean2d"], self.proj["conic"], opacity, self.proj["rgb"], bg=bg,
                                out=self.out, stream=stream)

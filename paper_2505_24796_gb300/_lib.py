@@ -28,8 +28,8 @@ class tcgs_camera(ctypes.Structure):
 
 
 class tcgs_render_opts(ctypes.Structure):
-    _fields_ = [("precision", c_int32), ("alpha_max", c_float), ("early_cull", c_int32), ("tile_stats", c_void_p),
-                ("device_status", c_void_p)]
+    _fields_ = [("precision", c_int32), ("alpha_max", c_float), ("early_cull", c_int32), ("tile_cull", c_int32),
+                ("tile_stats", c_void_p), ("device_status", c_void_p)]
 
 
 # name -> (restype, argtypes); the same names and order as include/tcgs.h

@@ -1,44 +1,56 @@
 // render_tc.cu -- conditional alpha-blending with the exponent on 5th-generation tensor cores:
 // EarlyCull (Sec. 4.1) + Frag2Mat (Sec. 4.2, Eq. 18) + G2L (Sec. 4.3).
 //
-// Mapping on sm_103a.  One CTA of 128 threads renders one half tile (16 x 8 pixels) and
-// walks its tile's sorted list in batches of 64 Gaussians:
-//   - U (128 pixels x K, f16) is built once in shared memory: the tile-local pixel vectors
+// Mapping on sm_103a.  One CTA of 256 threads renders one 16 x 16 tile; each of its 8 warps owns an
+// 8 x 4 pixel block.  The tile's sorted list is walked in batches of kN = 32 Gaussians:
+//   - U (256 pixels x 16, f16) is built once in shared memory: the tile-local pixel vectors
 //     u = [1, dx, dy, dx^2, dx dy, dy^2] with dx, dy in {+-0.5, ..., +-7.5}, exact in FP16;
-//   - per batch, 64 threads build V (64 Gaussians x K, f16) in shared memory from the
-//     Gaussians' tile-local v = [ln o - 1/2 dmu^T Q dmu, (Q dmu)_x, (Q dmu)_y, -1/2 s11, -s12,
-//     -1/2 s22] (Eq. 12 in G2L coordinates), scaled by log2(e) so the MMA yields log2(alpha);
-//   - one elected thread issues a single tcgen05.mma (M = 128, N = 64, K = 16, FP32 accumulator
-//     in TMEM) and commits it to an mbarrier;
-//   - each warp reads its 32 TMEM lanes with tcgen05.ld.32x32b: thread i receives pixel i's 64
-//     exponents, in list order, in registers, which is exactly the layout the front-to-back
-//     blend needs (no transpose, no cross-lane scan);
-//   - EarlyCull compares log2(alpha) with -log2(255) before ex2; survivors are blended in FP32.
+//   - a loader warp gathers each batch's Gaussians one batch ahead (registers), and stages their
+//     tile-local parameters, colours and V (32 Gaussians x 16, f16) in shared memory, V from the
+//     tile-local v = [ln o - 1/2 dmu^T Q dmu, (Q dmu)_x, (Q dmu)_y, -1/2 s11, -s12, -1/2 s22]
+//     (Eq. 12 in G2L coordinates) scaled by log2(e), so the MMA yields log2(alpha);
+//   - one elected thread issues two tcgen05.mma (M = 128 rows each, N = 32, K = 16, FP32
+//     accumulators in TMEM) against the same V and commits them to an mbarrier;
+//   - each warp marks, one batch ahead, the Gaussians that can reach alpha >= 1/255 anywhere in its
+//     block (exact minimum of the conic form over the block), then walks only its marked columns
+//     (a warp-uniform loop), reading each with tcgen05.ld.32x32b.x1: every thread receives its own
+//     pixel's exponent, in list order, which is the layout the front-to-back blend needs (no
+//     transpose, no cross-lane scan);
+//   - EarlyCull compares log2(alpha) with -log2(255) before ex2; survivors are blended in FP32,
+//     branch-free (selects), so a warp never diverges inside the walk.
 // Two precisions share the kernel:
 //   TC_FP16        the paper's K = 8 layout (v0 / 3 in three slots, u's 1 in three slots),
 //   TC_FP16_SPLIT  v = v_hi + v_lo (both FP16) with u duplicated: 12 of the 16 K slots,
 //                  same single MMA, about 22-bit accuracy of v.
+// The block marks only skip list entries that Algorithm 1 would cull at every pixel of the block
+// (the minimum over the block's pixel-centre rectangle bounds every pixel), so the image is that of
+// Algorithm 1; with tile_cull = 0 every entry is walked.
 // Every mbarrier wait is bounded; on a timeout the CTA records TCGS_ERR_TIMEOUT, stops, and still
-// releases its TMEM.
+// releases its TMEM; an MMA issued for a batch that is not walked is waited for before release.
+// Two accumulator buffers let the MMAs of batch k+1 run while batch k is walked; only thread 0 polls
+// the mbarrier, the others wait in a hardware barrier.
 #include "common.cuh"
 
 namespace tcgs {
 namespace {
 
-constexpr int kTcThreads = 128;
-constexpr int kTcN = 64;
-constexpr uint32_t kTmemCols = 64;
-constexpr int kSmemA = 0;          // U: 128 x 16 f16 = 4096 B
-constexpr int kSmemB = 4096;       // V: 64 x 16 f16 = 2048 B
-constexpr int kSmemC = 6144;       // colours: 64 x float4 = 1024 B
-constexpr int kSmemUsed = 7168;
-constexpr int kSmemDyn = 30 * 1024;  // keeps <= 7 CTAs per SM, so 7 x 64 TMEM columns always fit
-constexpr float kMaxDp = 10.606601717798213f;   // largest |pixel - tile centre| = 7.5 sqrt(2)
-constexpr float kCulledV = -30000.f;             // FP16-finite exponent of a batch slot that cannot pass
+constexpr int kConsumerWarps = 8;      // 8 warps of 8 x 4 pixels = one 16 x 16 tile, one thread per pixel
+constexpr int kTcThreads = 32 * (kConsumerWarps + 1);   // + one producer warp
+constexpr int kN = 32;                 // Gaussians per MMA batch (UMMA N; slot = producer lane)
+constexpr uint32_t kTmemCols = 4 * kN; // 2 accumulator buffers x 2 row halves
+constexpr int kVBytes = kN * 32;       // one V buffer: 32 x 16 f16
+constexpr int kPBytes = kN * 48;       // one parameter buffer: 3 float4 per slot
+constexpr int kSmemA = 0;              // U: 256 x 16 f16 = 8192 B (two 128-row halves)
+constexpr int kSmemB = 8192;           // V: 3 buffers
+constexpr int kSmemP = kSmemB + 3 * kVBytes;   // slot parameters and colours: 3 buffers
+// 46 KB of dynamic shared memory caps residency at 4 CTAs per SM (4 x 47 KB <= 228 KB < 5 x 47 KB),
+// so 4 x 128 TMEM columns always fit in the 512 available and tcgen05.alloc never waits
+constexpr int kSmemDyn = 46 * 1024;
+constexpr float kCulledV = -30000.f;   // FP16-finite exponent of a slot that no pixel can use
 
-// Byte offset of element (row, k) of a K-major f16 operand in the canonical no-swizzle layout:
-// 8-row x 16-byte core matrices, K-direction core matrices 128 B apart (LBO), 8-row groups 256 B
-// apart (SBO).
+// Byte offset of the 16-byte chunk kchunk (K elements 8 kchunk .. 8 kchunk + 7) of row `row` of a
+// K-major f16 operand in the canonical no-swizzle layout: 8-row x 16-byte core matrices,
+// K-direction core matrices 128 B apart (LBO), 8-row groups 256 B apart (SBO).
 __device__ __forceinline__ uint32_t canon_off(int row, int kchunk) {
     return (uint32_t)((row >> 3) * 256 + kchunk * 128 + (row & 7) * 16);
 }
@@ -59,7 +71,7 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
 
 // Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = F16 (0), both K-major,
 // N >> 3 at [17,23), M >> 4 at [24,29).
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
@@ -84,6 +96,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return r;
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile(
@@ -100,6 +119,30 @@ __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
     return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
+// Smallest value of q(p) = (m - p)^T Q (m - p) over the rectangle [x0, x1] x [y0, y1] of pixel
+// centres, Q = [[a, b], [b, c]] positive definite: 0 when m is inside, otherwise the smallest of the
+// four edge minima (each a 1-D convex quadratic minimised at its clamped stationary point).
+__device__ __forceinline__ float min_q_over_box(float mx, float my, float a, float b, float c, float x0, float x1,
+                                                float y0, float y1) {
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
+    const float ia = 1.f / a, ic = 1.f / c;
+    float best = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float X = e ? x1 : x0;
+        const float dx = mx - X;
+        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
+        const float dy = my - y;
+        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+        const float Y = e ? y1 : y0;
+        const float ey = my - Y;
+        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
+        const float ex = mx - x;
+        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
+    }
+    return best;
+}
+
 struct TcParams {
     DevCamera cam;
     const uint32_t* ranges;
@@ -111,6 +154,7 @@ struct TcParams {
     float bg[3];
     float alpha_max;
     int split;
+    int tile_cull;
     float* img;
     float* T_final;
     uint32_t* n_contrib;
@@ -121,44 +165,96 @@ struct TcParams {
     float* dbg_beta;
 };
 
-template <bool kInspect>
+// Gaussian data of one batch slot, held in the producer's registers one batch ahead of its use.
+struct Slot {
+    float mx, my, s11, s12, s22, o, r, g, b;
+    bool valid;
+};
+
+__device__ __forceinline__ Slot load_slot(const TcParams& p, uint32_t g, bool valid, bool colour) {
+    Slot d;
+    d.valid = valid;
+    if (valid) {
+        const float2 m = reinterpret_cast<const float2*>(p.mean2d)[g];
+        d.mx = m.x; d.my = m.y;
+        d.s11 = p.conic[3 * g]; d.s12 = p.conic[3 * g + 1]; d.s22 = p.conic[3 * g + 2];
+        d.o = p.opacity[g];
+        if (colour) { d.r = p.rgb[3 * g]; d.g = p.rgb[3 * g + 1]; d.b = p.rgb[3 * g + 2]; }
+        else { d.r = d.g = d.b = 0.f; }
+    } else {
+        d.mx = d.my = d.s11 = d.s12 = d.s22 = d.r = d.g = d.b = 0.f;
+        d.o = 1.f;
+    }
+    return d;
+}
+
+// Smallest q(p) = (m - p)^T Q (m - p) over a rectangle of pixel centres, with the reciprocals of the
+// diagonal of Q precomputed (see min_q_over_box).
+__device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float b, float c, float ia, float ic,
+                                             float x0, float x1, float y0, float y1) {
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
+    float best = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float X = e ? x1 : x0;
+        const float dx = mx - X;
+        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
+        const float dy = my - y;
+        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+        const float Y = e ? y1 : y0;
+        const float ey = my - Y;
+        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
+        const float ex = mx - x;
+        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
+    }
+    return best;
+}
+
+template <bool kInspect, bool kStats>
 __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
-    __shared__ unsigned long long s_acc[2];
+    __shared__ int s_timeout;
+    __shared__ unsigned long long s_acc[3];
 
-    const int t = threadIdx.x, warp = t >> 5;
-    int tile = kInspect ? p.dbg_tiles[blockIdx.x >> 1] : (int)(blockIdx.x >> 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const bool producer = warp == kConsumerWarps;
+    int tile = kInspect ? p.dbg_tiles[blockIdx.x] : (int)blockIdx.x;
     bool tile_ok = true;
     if (kInspect && (tile < 0 || tile >= p.cam.grid_w * p.cam.grid_h)) {   // never index past the grid
         if (t == 0) set_status(p.status, TCGS_ERR_INVALID);
         tile = 0;
         tile_ok = false;
     }
-    const int half = blockIdx.x & 1;
     const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
-    const int lx = t & 15, ly = half * 8 + (t >> 4);
+    // consumer warp block (8 x 4 pixels) of the tile, and this thread's pixel; warps 0-3 cover rows
+    // 0-7 (MMA half 0, U rows 0-127), warps 4-7 rows 8-15 (half 1, U rows 128-255)
+    const int half = (warp >> 2) & 1;
+    const int bx = warp & 1, by = (warp >> 1) & 3;
+    const int lx = 8 * bx + (lane & 7), ly = 4 * by + (lane >> 3);
     const int px_i = tx * kTile + lx, py_i = ty * kTile + ly;
-    const bool inside = px_i < p.cam.width && py_i < p.cam.height;
+    const bool inside = !producer && px_i < p.cam.width && py_i < p.cam.height;
     const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);   // p(T)
+    // this warp's pixel-centre rectangle, tile-local
+    const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f;
+    const float by0 = 4.f * by - 7.5f, by1 = by0 + 3.f;
     uint8_t* sA = smem + kSmemA;
-    uint8_t* sB = smem + kSmemB;
-    float4* sC = reinterpret_cast<float4*>(smem + kSmemC);
-    const uint32_t mbar = smem_u32(&s_mbar);
+    const uint32_t mbar0 = smem_u32(&s_mbar[0]);
 
-    if (warp == 0) {
+    if (producer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (t == 0) {
-        mbar_init(mbar, 1);
-        s_acc[0] = s_acc[1] = 0ull;
-    }
-    {
-        // U row of this pixel (G2L: dp = p - p(T))
+        if (lane == 0) {
+            mbar_init(mbar0, 1);
+            mbar_init(mbar0 + 8, 1);
+            s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
+            s_timeout = 0;
+        }
+    } else {
+        // U row t = this thread's pixel (G2L: dp = p - p(T))
         const float dx = (float)lx + 0.5f - kTile / 2, dy = (float)ly + 0.5f - kTile / 2;
         __half u[16];
         const __half one = __float2half_rn(1.f), zero = __float2half_rn(0.f);
@@ -178,14 +274,6 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
         *reinterpret_cast<uint4*>(sA + canon_off(t, 0)) = c0;
         *reinterpret_cast<uint4*>(sA + canon_off(t, 1)) = c1;
     }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = s_tmem;
-    const uint64_t descA = make_desc(smem_u32(sA));
-    const uint64_t descB = make_desc(smem_u32(sB));
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
 
     const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
     uint32_t stop = end;
@@ -193,133 +281,233 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
         uint32_t lim = start + (uint32_t)p.dbg_max_n;
         stop = !tile_ok ? start : (lim < end ? lim : end);
     }
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0, n_eval = end - start, n_blend = 0, walked = 0, phase = 0;
-    bool done = !inside;
-    float thr = done ? __int_as_float(0x7f800000) : kBeta2Cull;
+    const uint32_t nbat = (stop - start + kN - 1) / kN;
 
-    for (uint32_t b0 = start; b0 < stop; b0 += kTcN) {
-        if (t < kTcN) {
-            // V row of Gaussian b0 + t (FP32 arithmetic, then FP16)
-            uint32_t idx = b0 + t;
-            float v[6] = {kCulledV, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (idx < stop) {
-                uint32_t g = p.ids[idx];
-                float2 m = reinterpret_cast<const float2*>(p.mean2d)[g];
-                float s11 = p.conic[3 * g], s12 = p.conic[3 * g + 1], s22 = p.conic[3 * g + 2];
-                float o = p.opacity[g];
-                if (!kInspect) col = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], 0.f);
-                float mx = m.x - cx, my = m.y - cy;   // G2L mean
-                float qx = s11 * mx + s12 * my, qy = s12 * mx + s22 * my;
-                float q0 = mx * qx + my * qy;
-                float lno = __logf(o);
-                // conservative whole-tile cull: ||dmu - dp||_Q >= sqrt(q0) - |dp| sqrt(lambda_max(Q))
-                float lam = 0.5f * (s11 + s22) + sqrtf(0.25f * (s11 - s22) * (s11 - s22) + s12 * s12);
-                float reach = sqrtf(fmaxf(q0, 0.f)) - kMaxDp * sqrtf(fmaxf(lam, 0.f));
-                float need = 2.f * (lno - kBetaCull);
-                bool hopeless = need <= 0.f || (reach > 0.f && reach * reach > 1.001f * need + 1e-3f);
-                if (!hopeless) {
+    // Producer: stage batch slot `lane` into buffer `buf`: tile-local parameters (with the
+    // reciprocals the block tests need) and colour, and the V row of the MMA.
+    auto stage = [&](const Slot& d, int buf) {
+        float4* sP = reinterpret_cast<float4*>(smem + kSmemP + buf * kPBytes);
+        float v[6] = {kCulledV, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float mx = 0.f, my = 0.f, lim = -1.f, ia = 0.f, ic = 0.f;
+        if (d.valid) {
+            mx = d.mx - cx; my = d.my - cy;   // G2L mean
+            const float lno = __logf(d.o);
+            // alpha >= 1/255 somewhere needs q <= 2 (ln o + ln 255); relative and absolute margins
+            // keep every test conservative under FP32 rounding
+            const float reach = 2.f * (lno - kBetaCull);
+            lim = reach > -1e-3f ? reach * 1.0001f + 1e-3f : -1.f;
+            if (lim >= 0.f) {
+                // V only for Gaussians that can reach the tile: ||dmu - dp||_Q >= sqrt(q0) -
+                // |dp| sqrt(lambda_max(Q)), |dp| <= 7.5 sqrt(2); their tile-local coefficients are
+                // then bounded and FP16 never overflows
+                const float qx = d.s11 * mx + d.s12 * my, qy = d.s12 * mx + d.s22 * my;
+                const float q0 = fmaxf(mx * qx + my * qy, 0.f);
+                const float dd = 0.25f * (d.s11 - d.s22) * (d.s11 - d.s22) + d.s12 * d.s12;
+                const float lam = fmaxf(0.5f * (d.s11 + d.s22) + dd * rsqrtf(fmaxf(dd, 1e-30f)), 0.f);
+                const float gap = q0 * rsqrtf(fmaxf(q0, 1e-30f)) - 10.606601717798213f * lam * rsqrtf(fmaxf(lam, 1e-30f));
+                if (!(gap > 0.f && gap * gap > 1.01f * lim + 1e-2f)) {   // looser than any block test
                     v[0] = (lno - 0.5f * q0) * kLog2e;
                     v[1] = qx * kLog2e;
                     v[2] = qy * kLog2e;
-                    v[3] = -0.5f * s11 * kLog2e;
-                    v[4] = -s12 * kLog2e;
-                    v[5] = -0.5f * s22 * kLog2e;
+                    v[3] = -0.5f * d.s11 * kLog2e;
+                    v[4] = -d.s12 * kLog2e;
+                    v[5] = -0.5f * d.s22 * kLog2e;
+                    ia = __fdividef(1.f, d.s11);
+                    ic = __fdividef(1.f, d.s22);
+                } else {
+                    lim = -1.f;   // cannot reach the tile: no block test passes
                 }
             }
-            __half h[16];
+        }
+        sP[3 * lane] = make_float4(mx, my, d.s11, d.s12);
+        sP[3 * lane + 1] = make_float4(d.s22, lim, ia, ic);
+        sP[3 * lane + 2] = make_float4(d.r, d.g, d.b, 0.f);
+        uint8_t* sB = smem + kSmemB + buf * kVBytes;
+        __half h[16];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
-            if (p.split) {
+        for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
+        if (p.split) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    __half hi = __float2half_rn(v[k]);
-                    h[k] = hi;
-                    h[6 + k] = __float2half_rn(v[k] - __half2float(hi));
-                }
-                h[12] = h[13] = h[14] = h[15] = __float2half_rn(0.f);
-            } else {
-                __half third = __float2half_rn(v[0] * (1.f / 3.f));
-                h[0] = h[1] = h[2] = third;
-#pragma unroll
-                for (int k = 1; k < 6; ++k) h[2 + k] = __float2half_rn(v[k]);
-#pragma unroll
-                for (int k = 8; k < 16; ++k) h[k] = __float2half_rn(0.f);
+            for (int k = 0; k < 6; ++k) {
+                const __half hi = __float2half_rn(v[k]);
+                h[k] = hi;
+                h[6 + k] = __float2half_rn(v[k] - __half2float(hi));
             }
-            uint4 c0 = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-            uint4 c1 = make_uint4(pack2(h[8], h[9]), pack2(h[10], h[11]), pack2(h[12], h[13]), pack2(h[14], h[15]));
-            *reinterpret_cast<uint4*>(sB + canon_off(t, 0)) = c0;
-            *reinterpret_cast<uint4*>(sB + canon_off(t, 1)) = c1;
-            sC[t] = col;
-            fence_async_smem();
+            h[12] = h[13] = h[14] = h[15] = __float2half_rn(0.f);
+        } else {
+            const __half third = __float2half_rn(v[0] * (1.f / 3.f));
+            h[0] = h[1] = h[2] = third;
+#pragma unroll
+            for (int k = 1; k < 6; ++k) h[2 + k] = __float2half_rn(v[k]);
+#pragma unroll
+            for (int k = 8; k < 16; ++k) h[k] = __float2half_rn(0.f);
+        }
+        uint4 c0 = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+        uint4 c1 = make_uint4(pack2(h[8], h[9]), pack2(h[10], h[11]), pack2(h[12], h[13]), pack2(h[14], h[15]));
+        *reinterpret_cast<uint4*>(sB + canon_off(lane, 0)) = c0;
+        *reinterpret_cast<uint4*>(sB + canon_off(lane, 1)) = c1;
+        fence_async_smem();
+    };
+    // Consumer warps: which slots of buffer `buf` can reach alpha >= 1/255 somewhere in this warp's
+    // 8 x 4 block (exact minimum of the conic form over the block's pixel centres).
+    auto block_mask = [&](int buf) -> uint32_t {
+        const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + buf * kPBytes);
+        const float4 a = sP[3 * lane], b = sP[3 * lane + 1];
+        bool act = b.y >= 0.f;
+        if (act && p.tile_cull) act = min_q_box_r(a.x, a.y, a.z, a.w, b.x, b.z, b.w, bx0, bx1, by0, by1) <= b.y;
+        return __ballot_sync(0xffffffffu, act);
+    };
+    // Producer lane 0: both 128-row halves of U against the same V, committed to one mbarrier.
+    auto issue_mma = [&](uint32_t k) {
+        tc_fence_after();
+        const int vb = (int)(k % 3u), tb = (int)(k & 1u);
+        const uint64_t descB = make_desc(smem_u32(smem + kSmemB + vb * kVBytes));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t descA = make_desc(smem_u32(sA + h * 4096));
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                    s_tmem + (uint32_t)(tb * 2 * kN + h * kN)),
+                "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         mbar0 + 8u * (uint32_t)tb)
+                     : "memory");
+    };
+
+    // producer registers: `nxt` holds the data of the batch to stage next, `nid` the ids after that
+    Slot nxt;
+    uint32_t nid = 0;
+    auto prefetch = [&](uint32_t kb) {   // data of batch kb (ids already in nid), ids of batch kb + 1
+        const uint32_t i = start + kb * kN + lane;
+        nxt = load_slot(p, nid, i < stop, !kInspect);
+        const uint32_t i2 = i + kN;
+        if (i2 < stop) nid = p.ids[i2];
+    };
+    if (producer) {
+        if (start + lane < stop) nid = p.ids[start + lane];
+        prefetch(0);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();   // U visible to the tensor core, TMEM address and mbarriers published
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0, n_eval = end - start, n_blend = 0, cols = 0;
+    bool done = !inside;
+    const float kInf = __int_as_float(0x7f800000);
+    float thr = done ? kInf : kBeta2Cull;
+    uint32_t mask_cur = 0;
+    uint32_t phase_bits = 0;   // producer lane 0: completed-phase parity of the two mbarriers
+
+    auto wait_mma = [&](uint32_t k) -> bool {   // producer lane 0
+        const uint32_t tb = k & 1u;
+        const bool ok = mbar_wait(mbar0 + 8u * tb, (phase_bits >> tb) & 1u);
+        phase_bits ^= 1u << tb;
+        return ok;
+    };
+
+    // prologue: batches 0 and 1 staged, MMA 0 complete, MMA 1 issued, masks of batch 0 known
+    if (nbat > 0) {
+        if (producer) {
+            stage(nxt, 0);
+            if (nbat > 1) prefetch(1);
         }
         tc_fence_before();
         __syncthreads();
-        if (t == 0) {
-            tc_fence_after();
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
-                : "memory");
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                         : "memory");
-        }
-        bool ok = mbar_wait(mbar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (t == 0) set_status(p.status, TCGS_ERR_TIMEOUT);
-            break;
-        }
-        tc_fence_after();
-        uint32_t r[2 * 32];
-        tmem_ld32(taddr, r);
-        tmem_ld32(taddr + 32, r + 32);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const uint32_t nb = stop - b0 < (uint32_t)kTcN ? stop - b0 : (uint32_t)kTcN;
-        walked += nb;
-        if (kInspect) {
-            const int pix = half * 128 + t;
-            float* out = p.dbg_beta + ((size_t)(blockIdx.x >> 1) * 256 + pix) * p.dbg_max_n;
-            for (uint32_t j = 0; j < nb; ++j) out[b0 - start + j] = __uint_as_float(r[j]) * 0.6931471805599453f;
+        if (producer) {
+            if (lane == 0) issue_mma(0);
+            if (nbat > 1) {
+                stage(nxt, 1);
+                if (nbat > 2) prefetch(2);
+            }
+            if (lane == 0 && !wait_mma(0)) s_timeout = 1;
         } else {
+            mask_cur = block_mask(0);
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (producer && lane == 0 && nbat > 1 && !s_timeout) issue_mma(1);
+    }
+    bool stopped = nbat > 0 && s_timeout;
+    for (uint32_t k = 0; k < nbat && !stopped; ++k) {
+        // window: consumers walk batch k while the producer stages batch k + 2 and waits for MMA k + 1
+        if (producer) {
+            if (k + 2 < nbat) {
+                stage(nxt, (int)((k + 2) % 3u));
+                if (k + 3 < nbat) prefetch(k + 3);
+            }
+            if (lane == 0 && k + 1 < nbat && !wait_mma(k + 1)) s_timeout = 1;
+        } else if (kInspect) {
+            const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
+            uint32_t r[32];
+            tmem_ld32(taddr, r);
+            tmem_wait_ld();
+            const uint32_t b0 = start + k * kN;
+            const uint32_t nb = stop - b0 < (uint32_t)kN ? stop - b0 : (uint32_t)kN;
+            const int pix = ly * kTile + lx;
+            float* out = p.dbg_beta + ((size_t)blockIdx.x * 256 + pix) * p.dbg_max_n + (b0 - start);
 #pragma unroll
-            for (int j = 0; j < kTcN; ++j) {
-                const float b2 = __uint_as_float(r[j]);
-                if (b2 >= thr) {   // EarlyCull: log2(alpha) against -log2(255) before ex2
-                    const float a = fminf(p.alpha_max, ex2_approx(b2));
-                    const float Tn = fmaf(-a, T, T);
-                    if (Tn < kTmin) {
-                        thr = __int_as_float(0x7f800000);
-                        done = true;
-                        n_eval = b0 + j + 1 - start;
-                    } else {
-                        const float4 c = sC[j];
-                        const float w = a * T;
-                        C0 = fmaf(c.x, w, C0);
-                        C1 = fmaf(c.y, w, C1);
-                        C2 = fmaf(c.z, w, C2);
-                        T = Tn;
-                        last = b0 + j + 1 - start;
-                        ++n_blend;
-                    }
+            for (int j = 0; j < kN; ++j)
+                if ((uint32_t)j < nb) out[j] = __uint_as_float(r[j]) * 0.6931471805599453f;
+        } else {
+            // walk this warp's marked list entries, in list order
+            const uint32_t b0 = start + k * kN;
+            const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
+            const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + (k % 3u) * kPBytes);
+            uint32_t m = __all_sync(0xffffffffu, done) ? 0u : mask_cur;
+            if (kStats) cols += __popc(m);
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const float b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
+                tmem_wait_ld();
+                const bool pass = b2 >= thr;                       // EarlyCull, log2 units
+                const float a = fminf(p.alpha_max, ex2_approx(b2));
+                const float Tn = fmaf(-a, T, T);
+                const bool term = pass && (Tn < kTmin);           // Algorithm 1: terminate, unblended
+                const bool blend = pass && !term;
+                const float4 c = sP[3 * j + 2];
+                const float w = blend ? a * T : 0.f;
+                C0 = fmaf(c.x, w, C0);
+                C1 = fmaf(c.y, w, C1);
+                C2 = fmaf(c.z, w, C2);
+                T = blend ? Tn : T;
+                const uint32_t pos = b0 + (uint32_t)j + 1u - start;
+                last = blend ? pos : last;
+                if (kStats) {
+                    n_eval = term ? pos : n_eval;
+                    n_blend += blend ? 1u : 0u;
                 }
+                thr = term ? kInf : thr;
+                done = done || term;
             }
         }
         tc_fence_before();
-        if (!kInspect) {
-            if (!__syncthreads_or(!done)) break;
-        } else {
-            __syncthreads();
+        const bool more = __syncthreads_or(!done);   // batch k walked, batch k+2 staged, MMA k+1 done
+        tc_fence_after();
+        if (s_timeout) {
+            if (t == 0) set_status(p.status, TCGS_ERR_TIMEOUT);
+            break;
+        }
+        if (!kInspect && !more) break;
+        if (producer) {
+            if (lane == 0 && k + 2 < nbat) issue_mma(k + 2);
+        } else if (k + 1 < nbat) {
+            mask_cur = __all_sync(0xffffffffu, done) ? 0u : block_mask((int)((k + 1) % 3u));
         }
     }
+    // every MMA issued has been waited for: MMA k + 2 is only issued after the walk of batch k
+    // continues, and waited for in the next window, so TMEM is idle here
+    if (stopped && t == 0) set_status(p.status, TCGS_ERR_TIMEOUT);
 
-    if (kInspect) {
-        const int pix = half * 128 + t;
-        float* out = p.dbg_beta + ((size_t)(blockIdx.x >> 1) * 256 + pix) * p.dbg_max_n;
-        for (int j = (int)(stop - start); j < p.dbg_max_n; ++j) out[j] = -__int_as_float(0x7f800000);
-    } else {
+    if (!kInspect) {
         if (inside) {
             size_t pix = (size_t)py_i * p.cam.width + px_i;
             size_t plane = (size_t)p.cam.width * p.cam.height;
@@ -329,22 +517,27 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
             p.T_final[pix] = T;
             p.n_contrib[pix] = last;
         }
-        if (p.stats) {
+        if (kStats) {
             if (inside) {
                 atomicAdd(&s_acc[0], (unsigned long long)n_blend);
                 atomicAdd(&s_acc[1], (unsigned long long)(n_eval - n_blend));
             }
+            if (lane == 0 && !producer) atomicAdd(&s_acc[2], (unsigned long long)cols * 32ull);
         }
+    } else if (!producer) {
+        const int pix = ly * kTile + lx;
+        float* out = p.dbg_beta + ((size_t)blockIdx.x * 256 + pix) * p.dbg_max_n;
+        for (int j = (int)(stop - start); j < p.dbg_max_n; ++j) out[j] = -kInf;
     }
     tc_fence_before();
     __syncthreads();
-    if (!kInspect && p.stats && t == 0) {
+    if (kStats && t == 0) {
         atomicAdd(&p.stats[4 * tile + 0], (uint32_t)s_acc[0]);
         atomicAdd(&p.stats[4 * tile + 1], (uint32_t)s_acc[1]);
-        atomicAdd(&p.stats[4 * tile + 2], walked * (uint32_t)kTcThreads);
-        if (half == 0) atomicAdd(&p.stats[4 * tile + 3], end - start);
+        atomicAdd(&p.stats[4 * tile + 2], (uint32_t)s_acc[2]);
+        atomicAdd(&p.stats[4 * tile + 3], end - start);
     }
-    if (warp == 0) {
+    if (producer) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
@@ -365,17 +558,17 @@ bool device_is_sm103() {
     return g_device_ok;
 }
 
-bool g_attr_set[2] = {false, false};
+bool g_attr_set[2][2] = {{false, false}, {false, false}};
 
-template <bool kInspect>
+template <bool kInspect, bool kStats>
 tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
-    if (!g_attr_set[kInspect]) {
-        if (cudaFuncSetAttribute(k_render_tc<kInspect>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) !=
-            cudaSuccess)
+    if (!g_attr_set[kInspect][kStats]) {
+        if (cudaFuncSetAttribute(k_render_tc<kInspect, kStats>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemDyn) != cudaSuccess)
             return TCGS_ERR_CUDA;
-        g_attr_set[kInspect] = true;
+        g_attr_set[kInspect][kStats] = true;
     }
-    k_render_tc<kInspect><<<blocks, kTcThreads, kSmemDyn, s>>>(p);
+    k_render_tc<kInspect, kStats><<<blocks, kTcThreads, kSmemDyn, s>>>(p);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
@@ -388,12 +581,12 @@ TcParams base_params(const tcgs_camera* cam, int precision, const uint32_t* tile
     p.ranges = tile_ranges; p.ids = ids; p.mean2d = mean2d; p.conic = conic; p.opacity = opacity;
     p.split = precision == TCGS_TC_FP16_SPLIT;
     p.alpha_max = 0.99f;
+    p.tile_cull = 1;
     return p;
 }
 
 }  // namespace
 
-static_assert(kSmemUsed <= kSmemDyn, "shared memory layout");
 
 tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opts, const uint32_t* tile_ranges,
                              const uint32_t* ids_sorted, const float* mean2d, const float* conic,
@@ -406,8 +599,9 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
     p.alpha_max = opts->alpha_max;
     p.img = img; p.T_final = T_final; p.n_contrib = n_contrib;
     p.stats = opts->tile_stats; p.status = opts->device_status;
+    p.tile_cull = opts->tile_cull;
     int tiles = p.cam.grid_w * p.cam.grid_h;
-    return launch_tc<false>(p, 2 * tiles, s);
+    return p.stats ? launch_tc<false, true>(p, tiles, s) : launch_tc<false, false>(p, tiles, s);
 }
 
 }  // namespace tcgs
@@ -459,5 +653,5 @@ extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precis
     TcParams p = base_params(cam, precision, tile_ranges, ids_sorted, mean2d, conic, opacity);
     p.status = device_status;
     p.dbg_tiles = tiles; p.dbg_max_n = max_n; p.dbg_beta = beta_out;
-    return launch_tc<true>(p, 2 * n_tiles, (cudaStream_t)stream);
+    return launch_tc<true, false>(p, n_tiles, (cudaStream_t)stream);
 }

@@ -302,3 +302,34 @@ def test_autograd_function_matches_backward(tc):
     for p, k in zip(params, ("dmean2d", "dconic", "dopacity", "drgb")):
         a = p.grad.cpu().numpy().reshape(ref[k].shape)
         np.testing.assert_allclose(a, ref[k], rtol=1e-3, atol=1e-4 * np.abs(ref[k]).max())
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+@pytest.mark.parametrize("precision", ["tc_fp16_split", "tc_fp16"])
+def test_tc_block_culling_changes_nothing(tc, name, make, precision):
+    """The per-block skip only drops list entries whose exact exponent is below -ln 255 (with a margin
+    of about 5e-4) at every pixel of the block.  For the split layout (exponent error ~1e-5) the image
+    is therefore bit-identical with and without the skip; the paper's K = 8 layout has exponent errors
+    up to ~0.1, which can lift such an entry over the threshold when it is not skipped, so there only
+    a handful of pixels may differ.  Fewer entries are executed either way."""
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    nt = b["ranges"].shape[0]
+    res = {}
+    for cull in (False, True):
+        stats = torch.zeros(nt, 4, dtype=torch.int32, device=DEV)
+        out = tc.tcgs_render_fwd(cam, tc.render_opts(precision, tile_stats=stats, tile_cull=cull), g["ranges"],
+                                 g["ids"], g["mean2d"], g["conic"], g["opacity"], g["rgb"])
+        torch.cuda.synchronize()
+        res[cull] = ({k: v.cpu().numpy() for k, v in out.items()}, stats.cpu().numpy().astype(np.int64))
+    if precision == "tc_fp16_split":
+        for k in ("img", "T_final", "n_contrib"):
+            np.testing.assert_array_equal(res[True][0][k], res[False][0][k])
+        np.testing.assert_array_equal(res[True][1][:, :2], res[False][1][:, :2])
+    else:
+        diff = (res[True][0]["img"] != res[False][0]["img"]).any(axis=0)
+        assert diff.mean() < 1e-2
+        # skipping only removes entries that are culled in exact arithmetic: never further from the oracle
+        assert psnr(res[True][0]["img"], o["img"]) >= psnr(res[False][0]["img"], o["img"]) - 0.05
+    assert res[True][1][:, 2].sum() < res[False][1][:, 2].sum()
