@@ -118,6 +118,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ 
     if (d == 0) digit_total_next[t] = 0u;
 }
 
+// Stable scatter of one 8-bit digit.  Per 2048-key tile: warp-level ranks (__match_any_sync), a
+// per-digit prefix over the warps, keys regrouped by digit in shared memory, then written out so
+// that consecutive threads write consecutive addresses of each digit's run (coalesced).
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
@@ -125,28 +128,31 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
                                                             const uint32_t* n_dev, int shift, int G,
                                                             const uint32_t* __restrict__ offsets) {
     __shared__ uint32_t wcnt[kWarps][kRadix];
-    __shared__ uint32_t boff[kRadix];
+    __shared__ uint32_t boff[kRadix];     // next global position of each digit for this block
+    __shared__ uint32_t tstart[kRadix];   // tile-local start of each digit's run
+    __shared__ uint32_t ws[kWarps];
+    __shared__ uint32_t sk[kTileItems], sv[kTileItems];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     uint32_t lo, hi;
     block_range(load_n(n_host, n_dev), G, lo, hi);
     boff[t] = offsets[(size_t)t * G + blockIdx.x];
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (uint32_t tile = lo; tile < hi; tile += kTileItems) {
+        const uint32_t tile_n = hi - tile < (uint32_t)kTileItems ? hi - tile : (uint32_t)kTileItems;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) wcnt[w][t] = 0;
         __syncthreads();
-        uint32_t k[kItems], v[kItems], rank[kItems];
-        uint32_t dg[kItems];
+        uint32_t k[kItems], v[kItems], rank[kItems], dg[kItems];
         const uint32_t base = tile + (uint32_t)warp * (32 * kItems);
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
-            uint32_t i = base + r * 32 + lane;
-            bool valid = i < hi;
+            const uint32_t i = base + r * 32 + lane;
+            const bool valid = i < hi;
             k[r] = valid ? keys_in[i] : 0u;
             v[r] = valid ? vals_in[i] : 0u;
-            uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u | lane);
+            const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u | lane);
             dg[r] = d;
-            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
             uint32_t before = 0;
             if (valid) before = wcnt[warp][d];
             __syncwarp();
@@ -155,24 +161,39 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
             rank[r] = before + __popc(peers & lt_mask);
         }
         __syncthreads();
-        uint32_t run = boff[t];
+        // digit t: exclusive prefix over warps, the tile's count, and the tile-local run start
+        uint32_t total = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            uint32_t c = wcnt[w][t];
-            wcnt[w][t] = run;
-            run += c;
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = total;
+            total += c;
         }
-        boff[t] = run;
+        uint32_t tile_total;
+        tstart[t] = block_exclusive_scan<uint32_t, kThreads>(total, ws, tile_total);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
             if (dg[r] < 0x100u) {
-                uint32_t pos = wcnt[warp][dg[r]] + rank[r];
-                keys_out[pos] = k[r];
-                vals_out[pos] = v[r];
+                const uint32_t lp = tstart[dg[r]] + wcnt[warp][dg[r]] + rank[r];
+                sk[lp] = k[r];
+                sv[lp] = v[r];
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) {
+            const uint32_t i = (uint32_t)t + (uint32_t)q * kThreads;
+            if (i < tile_n) {
+                const uint32_t key = sk[i];
+                const uint32_t d = (key >> shift) & 0xFFu;
+                const uint32_t gp = boff[d] + (i - tstart[d]);
+                keys_out[gp] = key;
+                vals_out[gp] = sv[i];
+            }
+        }
+        __syncthreads();
+        boff[t] += total;
     }
 }
 
@@ -254,6 +275,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_final(const uint32_t* __restr
     }
 }
 
+// Duplication in depth order, one warp per 32 consecutive depth-sorted Gaussians: their splats
+// occupy one contiguous output range, which the warp writes cooperatively (lane s writes splats
+// s, s + 32, ...), finding each splat's Gaussian by a 5-step shuffle search over the warp's
+// exclusive prefix of splat counts.  Writes are coalesced and big Gaussians do not serialise a thread.
 __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t P, const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint32_t* __restrict__ counts,
@@ -261,19 +286,53 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
                                                         const int32_t* __restrict__ radius,
                                                         uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ n_u32) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P || *n_u32 == 0u) return;
-    uint32_t g = order[i];
-    if (counts[g] == 0u) return;
-    float2 m = reinterpret_cast<const float2*>(mean2d)[g];
-    Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
-    uint32_t o = offsets[i];
-    for (int ty = rc.y0; ty <= rc.y1; ++ty)
-        for (int tx = rc.x0; tx <= rc.x1; ++tx) {
-            tile_keys[o] = (uint32_t)(ty * cam.grid_w + tx);
-            vals[o] = g;
-            ++o;
+    if (*n_u32 == 0u) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t g = 0, cnt = 0, x0 = 0, y0 = 0, rw = 1, off = 0;
+    if (i < P) {
+        g = order[i];
+        cnt = counts[g];
+        off = offsets[i];
+        if (cnt) {
+            const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
+            const Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
+            x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
         }
+    }
+    // warp exclusive prefix of the counts (the warp's splats are contiguous from lane 0's offset)
+    uint32_t pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= cnt;
+    const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
+    for (uint32_t s0 = 0; s0 < total; s0 += 32) {
+        const uint32_t sidx = s0 + (uint32_t)lane;
+        // owner = last lane whose prefix is <= sidx (lanes with zero count share a prefix with the
+        // next lane and are skipped because the search keeps the largest such lane)
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = owner + step;
+            const uint32_t pv = __shfl_sync(0xffffffffu, pre, cand & 31);
+            if (cand < 32 && pv <= sidx) owner = cand;
+        }
+        const uint32_t o_pre = __shfl_sync(0xffffffffu, pre, owner);
+        const uint32_t o_g = __shfl_sync(0xffffffffu, g, owner);
+        const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, owner);
+        const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, owner);
+        const uint32_t o_rw = __shfl_sync(0xffffffffu, rw, owner);
+        if (sidx < total) {
+            const uint32_t kk = sidx - o_pre;
+            const uint32_t ty = o_y0 + kk / o_rw, tx = o_x0 + kk % o_rw;
+            tile_keys[first + sidx] = ty * (uint32_t)cam.grid_w + tx;
+            vals[first + sidx] = o_g;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_ranges(const uint32_t* __restrict__ tile_keys,
