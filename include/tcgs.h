@@ -81,11 +81,13 @@ typedef struct {
     int32_t tile_cull;       /* TC paths: 1 = skip, per 8x4 pixel block, list entries whose Gaussian cannot
                                 reach alpha >= 1/255 at any pixel of the block (exact minimum of the conic
                                 form over the block; the image is unchanged); 0 = walk every entry */
-    uint32_t* tile_stats;    /* nullable device [num_tiles * 4], accumulated (+=) per tile:
+    uint32_t* tile_stats;    /* nullable device [num_tiles * 8], accumulated (+=) per tile:
                                 [0] blended fragments, [1] evaluated but not blended fragments
                                 (culled, plus the fragment that triggers termination),
                                 [2] fragment slots the kernel executed (pixels x list entries walked),
-                                [3] list length n(T) (added once per launch) */
+                                [3] list length n(T), [4] list entries the tile's CTA walked before all
+                                its pixels terminated, [5] the tile's CTA time in SM clock cycles / 64,
+                                [6], [7] reserved (0) */
     int32_t* device_status;  /* nullable device int32: set to a tcgs_status on a device-side error */
 } tcgs_render_opts;
 
@@ -192,6 +194,87 @@ TCGS_API tcgs_status tcgs_render_fwd(const tcgs_camera* cam /* host */, const tc
                             const float* conic, const float* opacity, const float* rgb,
                             const float* bg3 /* host */, float* img, float* T_final, uint32_t* n_contrib,
                             tcgs_stream stream);
+
+/* Largest number of views one batched launch can render. */
+#define TCGS_MAX_VIEWS 16
+
+/* One view of a batched render: its camera, its projection and sort outputs, and its outputs
+ * (all device pointers as in tcgs_render_fwd; tile_stats nullable, [num_tiles * 8]). */
+typedef struct {
+    tcgs_camera cam;
+    const uint32_t* tile_ranges;
+    const uint32_t* ids_sorted;
+    const float* mean2d;
+    const float* conic;
+    const float* rgb;
+    float* img;
+    float* T_final;
+    uint32_t* n_contrib;
+    uint32_t* tile_stats;
+} tcgs_view;
+
+/*
+ * Batched multi-view conditional alpha-blending with a persistent scheduler: a grid of resident
+ * CTAs (at most max_ctas when > 0) repeatedly takes the next work item from `queue` with an atomic
+ * counter and renders that tile exactly as tcgs_render_fwd does (same per-tile body, so every image
+ * is identical to a per-view launch whatever the queue order).  An item is (view << 16) | tile.
+ * The order of `queue` decides the schedule only: a longest-predicted-first order shortens the
+ * makespan when tile costs are uneven.  TC precisions only (FP16 or FP16_SPLIT).
+ * In:  n_views in [1, TCGS_MAX_VIEWS] views (host array of tcgs_view), opacity [P] shared by all
+ *      views, bg3 host float[3], queue: device [n_items] uint32.
+ * work_counter: device uint32, scratch (reset by the call on `stream`).
+ */
+TCGS_API tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view* views /* host */,
+                                             const tcgs_render_opts* opts /* host */, const float* opacity,
+                                             const float* bg3 /* host */, const uint32_t* queue, int32_t n_items,
+                                             uint32_t* work_counter, int32_t max_ctas, tcgs_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned tile-cost model for the batched renderer's queue (not part of the paper).  The paper has
+ * no counterpart: it is the scheduling layer a batched multi-view pipeline needs once each tile's
+ * alpha-blending is fast.  An MLP 8 -> 32 -> 32 -> 1 (ReLU, FP16 weights and activations, FP32
+ * accumulation) predicts log(tile cost) from per-tile statistics.
+ * Parameters (float32 masters, TCGS_MLP_PARAMS values): W1[32][8], b1[32], W2[32][32], b2[32],
+ * W3[32], b3.  The forward rounds every weight, the normalised input and both hidden activations
+ * to FP16; products and sums are FP32.
+ * ------------------------------------------------------------------------------------------- */
+#define TCGS_MLP_IN 8
+#define TCGS_MLP_HIDDEN 32
+#define TCGS_MLP_PARAMS 1377
+
+/* Per-tile features of one view, [num_tiles, 8] float32:
+ *   0 log(1 + n(T)), 1 mean opacity, 2 max opacity, 3 log(1 + depth span), 4 mean log det(conic),
+ *   5 log(1 + coverage) with coverage = sum over the list of |3-sigma square ∩ tile| / 256,
+ *   6 log(W H), 7 fraction of the tile's pixels inside the image (empty list: 0, 0, 0, 0, 0, 0, .). */
+TCGS_API tcgs_status tcgs_tile_features(const tcgs_camera* cam /* host */, const uint32_t* tile_ranges,
+                                        const uint32_t* ids_sorted, const float* mean2d, const float* conic,
+                                        const float* opacity, const float* depth, const int32_t* radius,
+                                        float* features, tcgs_stream stream);
+
+/* Feature normaliser of n rows of x [n, 8]: norm[0..7] = column means, norm[8..15] = 1 / std. */
+TCGS_API tcgs_status tcgs_feature_norm(const float* x, int32_t n, float* norm, tcgs_stream stream);
+
+/* y[i] = MLP((x[i] - norm[0..7]) * norm[8..15]) for n rows of x [n, 8]. */
+TCGS_API tcgs_status tcgs_mlp_fwd(const float* params, const float* norm, const float* x, int32_t n, float* y,
+                                  tcgs_stream stream);
+
+/* Gradient of L = (1/n) sum_i (MLP(x_i) - target_i)^2, accumulated (+=) into grad [TCGS_MLP_PARAMS];
+ * loss (nullable, device float) accumulates L.  The backward uses the forward's FP16-rounded values
+ * and passes through the rounding unchanged. */
+TCGS_API tcgs_status tcgs_mlp_bwd(const float* params, const float* norm, const float* x, const float* target,
+                                  int32_t n, float* grad, float* loss, tcgs_stream stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n_params parameters; grad is consumed (set to 0). */
+TCGS_API tcgs_status tcgs_adam_step(float* params, float* m, float* v, float* grad, int32_t n_params, float lr,
+                                    float beta1, float beta2, float eps, int32_t step, tcgs_stream stream);
+
+/* Bytes of device workspace tcgs_sched_order needs for n items (host function). */
+TCGS_API size_t tcgs_sched_order_workspace_size(int32_t n);
+
+/* queue_out = items ordered by decreasing cost (ties keep their input order): a stable LSD radix
+ * sort of the cost's order-preserving bits, 4 passes of 8 bits. */
+TCGS_API tcgs_status tcgs_sched_order(const float* cost, const uint32_t* items, int32_t n, uint32_t* queue_out,
+                                      void* workspace, size_t ws_bytes, tcgs_stream stream);
 
 /*
  * Backward of Algorithm 1 (C = sum_j c_j a_j T_j + bg T_final, Eq. 6) w.r.t. mean2d, conic,

@@ -23,8 +23,9 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS
 
 TILE = 16
 
-__all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc", "tcgs_render_fwd", "tcgs_render_bwd",
-           "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "TcgsError", "PRECISIONS",
+__all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
+           "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
+           "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "TcgsError", "PRECISIONS",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8"]
 
 
@@ -192,6 +193,96 @@ def tcgs_render_bwd(cam, opts, tile_ranges, ids_sorted, mean2d, conic, opacity, 
     return grads
 
 
+def tcgs_render_fwd_batched(views, opts, opacity, queue, bg=(0.0, 0.0, 0.0), counter=None, max_ctas=0,
+                            stream=None):
+    """Persistent multi-view render of the (view << 16 | tile) items of ``queue`` in that order.
+    ``views``: list of dicts with cam, tile_ranges, ids_sorted, mean2d, conic, rgb, img, T_final,
+    n_contrib and optional tile_stats (device tensors)."""
+    if not isinstance(opts, tcgs_render_opts):
+        opts = render_opts(**opts)
+    arr = (_lib.tcgs_view * len(views))()
+    for i, v in enumerate(views):
+        w = arr[i]
+        w.cam = _cam(v["cam"])
+        w.tile_ranges = _ptr(v["tile_ranges"], torch.int32, "tile_ranges")
+        w.ids_sorted = _ptr(v["ids_sorted"], torch.int32, "ids_sorted")
+        w.mean2d = _ptr(v["mean2d"], torch.float32, "mean2d")
+        w.conic = _ptr(v["conic"], torch.float32, "conic")
+        w.rgb = _ptr(v["rgb"], torch.float32, "rgb")
+        w.img = _ptr(v["img"], torch.float32, "img")
+        w.T_final = _ptr(v["T_final"], torch.float32, "T_final")
+        w.n_contrib = _ptr(v["n_contrib"], torch.int32, "n_contrib")
+        w.tile_stats = _ptr(v["tile_stats"], torch.int32, "tile_stats") if v.get("tile_stats") is not None else None
+    if counter is None:
+        counter = torch.zeros(1, dtype=torch.int32, device=opacity.device)
+    bg3 = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    check("tcgs_render_fwd_batched", _L().tcgs_render_fwd_batched(
+        len(views), arr, ctypes.byref(opts), _ptr(opacity, torch.float32, "opacity"), ctypes.cast(bg3, ctypes.c_void_p),
+        _ptr(queue, torch.int32, "queue"), queue.numel(), _ptr(counter, torch.int32, "counter"), int(max_ctas),
+        _stream(stream)))
+    return views
+
+
+def tcgs_tile_features(cam, tile_ranges, ids_sorted, mean2d, conic, opacity, depth, radius, out=None,
+                       stream=None) -> torch.Tensor:
+    c = _cam(cam)
+    nt = grid(c)[0] * grid(c)[1]
+    if out is None:
+        out = torch.empty(nt, _lib.TCGS_MLP_IN, device=mean2d.device)
+    f = torch.float32
+    check("tcgs_tile_features", _L().tcgs_tile_features(
+        ctypes.byref(c), _ptr(tile_ranges, torch.int32), _ptr(ids_sorted, torch.int32), _ptr(mean2d, f),
+        _ptr(conic, f), _ptr(opacity, f), _ptr(depth, f), _ptr(radius, torch.int32), _ptr(out, f), _stream(stream)))
+    return out
+
+
+def tcgs_feature_norm(x, out=None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(2 * _lib.TCGS_MLP_IN, device=x.device)
+    check("tcgs_feature_norm", _L().tcgs_feature_norm(_ptr(x, torch.float32, "x"), x.shape[0],
+                                                       _ptr(out, torch.float32), _stream(stream)))
+    return out
+
+
+def tcgs_mlp_fwd(params, norm, x, out=None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(x.shape[0], device=x.device)
+    f = torch.float32
+    check("tcgs_mlp_fwd", _L().tcgs_mlp_fwd(_ptr(params, f, "params"), _ptr(norm, f, "norm"), _ptr(x, f, "x"),
+                                             x.shape[0], _ptr(out, f), _stream(stream)))
+    return out
+
+
+def tcgs_mlp_bwd(params, norm, x, target, grad=None, loss=None, stream=None):
+    f = torch.float32
+    if grad is None:
+        grad = torch.zeros(_lib.TCGS_MLP_PARAMS, device=x.device)
+    check("tcgs_mlp_bwd", _L().tcgs_mlp_bwd(_ptr(params, f, "params"), _ptr(norm, f, "norm"), _ptr(x, f, "x"),
+                                             _ptr(target, f, "target"), x.shape[0], _ptr(grad, f, "grad"),
+                                             _ptr(loss, f, "loss") if loss is not None else None, _stream(stream)))
+    return grad, loss
+
+
+def tcgs_adam_step(params, m, v, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1, stream=None):
+    f = torch.float32
+    check("tcgs_adam_step", _L().tcgs_adam_step(_ptr(params, f), _ptr(m, f), _ptr(v, f), _ptr(grad, f),
+                                                 params.numel(), float(lr), float(beta1), float(beta2), float(eps),
+                                                 int(step), _stream(stream)))
+
+
+def tcgs_sched_order(cost, items, workspace=None, out=None, stream=None) -> torch.Tensor:
+    n = cost.numel()
+    ws_bytes = int(_L().tcgs_sched_order_workspace_size(n))
+    if workspace is None:
+        workspace = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=cost.device)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=cost.device)
+    check("tcgs_sched_order", _L().tcgs_sched_order(
+        _ptr(cost, torch.float32, "cost"), _ptr(items, torch.int32, "items"), n, _ptr(out, torch.int32),
+        _ptr(workspace, None, "workspace"), workspace.numel(), _stream(stream)))
+    return out
+
+
 def tcgs_frag2mat_beta(cam, precision, tile_ranges, ids_sorted, mean2d, conic, opacity, tiles, max_n,
                        device_status=None, stream=None) -> torch.Tensor:
     c = _cam(cam)
@@ -238,7 +329,8 @@ class Renderer:
                          status=torch.zeros(1, dtype=torch.int32, device=dev))
         self.out = dict(img=torch.empty(3, H, W, device=dev), T_final=torch.empty(H, W, device=dev),
                         n_contrib=torch.empty(H, W, dtype=torch.int32, device=dev))
-        self.stats = torch.zeros(self.num_tiles, 4, dtype=torch.int32, device=dev) if stats else None
+        self.stats = (torch.zeros(self.num_tiles, _lib.TILE_STATS_WORDS, dtype=torch.int32, device=dev)
+                      if stats else None)
         self.device_status = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def project(self, scene: dict, stream=None):

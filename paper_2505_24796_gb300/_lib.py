@@ -32,6 +32,17 @@ class tcgs_render_opts(ctypes.Structure):
                 ("tile_stats", c_void_p), ("device_status", c_void_p)]
 
 
+TCGS_MAX_VIEWS = 16
+TCGS_MLP_IN, TCGS_MLP_HIDDEN, TCGS_MLP_PARAMS = 8, 32, 1377
+TILE_STATS_WORDS = 8
+
+
+class tcgs_view(ctypes.Structure):
+    _fields_ = [("cam", tcgs_camera), ("tile_ranges", c_void_p), ("ids_sorted", c_void_p), ("mean2d", c_void_p),
+                ("conic", c_void_p), ("rgb", c_void_p), ("img", c_void_p), ("T_final", c_void_p),
+                ("n_contrib", c_void_p), ("tile_stats", c_void_p)]
+
+
 # name -> (restype, argtypes); the same names and order as include/tcgs.h
 P_CAM = ctypes.POINTER(tcgs_camera)
 P_OPT = ctypes.POINTER(tcgs_render_opts)
@@ -46,6 +57,14 @@ SIGNATURES = {
     "tcgs_bin_sort_noalloc": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, V, V, V, V]),
     "tcgs_render_fwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_render_bwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V]),
+    "tcgs_render_fwd_batched": (c_int32, [c_int32, V, P_OPT, V, V, V, c_int32, V, c_int32, V]),
+    "tcgs_tile_features": (c_int32, [P_CAM, V, V, V, V, V, V, V, V, V]),
+    "tcgs_feature_norm": (c_int32, [V, c_int32, V, V]),
+    "tcgs_mlp_fwd": (c_int32, [V, V, V, c_int32, V, V]),
+    "tcgs_mlp_bwd": (c_int32, [V, V, V, V, c_int32, V, V, V]),
+    "tcgs_adam_step": (c_int32, [V, V, V, V, c_int32, c_float, c_float, c_float, c_float, c_int32, V]),
+    "tcgs_sched_order_workspace_size": (c_size_t, [c_int32]),
+    "tcgs_sched_order": (c_int32, [V, V, c_int32, V, V, c_size_t, V]),
     "tcgs_frag2mat_beta": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int32, V, c_int32, V, V, V]),
 }
 

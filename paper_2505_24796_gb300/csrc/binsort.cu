@@ -483,6 +483,72 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     return TCGS_OK;
 }
 
+// ---------------------------------------------------------------- work-queue ordering
+
+namespace tcgs {
+namespace {
+
+__global__ void __launch_bounds__(kThreads) k_order_keys(const float* __restrict__ cost,
+                                                         const uint32_t* __restrict__ items, int n,
+                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                         uint32_t* __restrict__ digit_total0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0) digit_total0[threadIdx.x] = 0u;
+    if (i >= n) return;
+    keys[i] = ~orderable_bits(cost[i]);   // ascending keys = descending cost
+    vals[i] = items[i];
+}
+
+struct OrderWs {
+    uint32_t *k0, *v0, *k1, *v1, *hist, *digit_total;
+    size_t bytes;
+};
+
+inline OrderWs order_layout(char* base, int64_t n) {
+    OrderWs w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+    w.k0 = (uint32_t*)take(4 * n); w.v0 = (uint32_t*)take(4 * n);
+    w.k1 = (uint32_t*)take(4 * n); w.v1 = (uint32_t*)take(4 * n);
+    w.hist = (uint32_t*)take(4 * (size_t)kRadix * kMaxBlocks);
+    w.digit_total = (uint32_t*)take(4 * 2 * kRadix);
+    w.bytes = off;
+    return w;
+}
+
+}  // namespace
+}  // namespace tcgs
+
+extern "C" size_t tcgs_sched_order_workspace_size(int32_t n) {
+    if (n < 0) return 0;
+    return tcgs::order_layout(nullptr, n).bytes;
+}
+
+extern "C" tcgs_status tcgs_sched_order(const float* cost, const uint32_t* items, int32_t n, uint32_t* queue_out,
+                                        void* workspace, size_t ws_bytes, tcgs_stream stream) {
+    using namespace tcgs;
+    if (n < 0 || (n > 0 && (!cost || !items || !queue_out || !workspace)) ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return TCGS_ERR_INVALID;
+    if (n == 0) return TCGS_OK;
+    OrderWs o = order_layout((char*)workspace, n);
+    if (ws_bytes < o.bytes) return TCGS_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_order_keys<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(cost, items, n, o.k0, o.v0, o.digit_total);
+    count_launches(1);
+    Workspace w = {};
+    w.hist = o.hist;
+    w.digit_total = o.digit_total;
+    const int G = sort_blocks(n);
+    // 0 -> 1 -> 0 -> 1 -> out
+    radix_pass(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 0, G, w, 0, s);
+    radix_pass(o.k1, o.v1, o.k0, o.v0, (uint32_t)n, nullptr, 8, G, w, 1, s);
+    radix_pass(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 16, G, w, 2, s);
+    radix_pass(o.k1, o.v1, o.k0, queue_out, (uint32_t)n, nullptr, 24, G, w, 3, s);
+    TCGS_CHECK_LAUNCH();
+    return TCGS_OK;
+}
+
 // ---------------------------------------------------------------- allocation-free variant
 //
 // The scratch array every tcgs_bin_sort_noalloc call works in.  Host code must not pass its name

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_fp32(FwdParams p) {
     const float px = px_i + 0.5f, py = py_i + 0.5f;
     const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
 
+    const long long t_start = clock64();
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0, n_eval = end - start, n_blend = 0;
     bool done = !inside;
@@ -100,10 +101,13 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_fp32(FwdParams p) {
         }
         __syncthreads();
         if (t == 0) {
-            atomicAdd(&p.stats[4 * tile + 0], (uint32_t)s_acc[0]);
-            atomicAdd(&p.stats[4 * tile + 1], (uint32_t)s_acc[1]);
-            atomicAdd(&p.stats[4 * tile + 2], walked * (uint32_t)kFwdThreads);
-            atomicAdd(&p.stats[4 * tile + 3], end - start);
+            uint32_t* st = p.stats + 8 * tile;
+            atomicAdd(&st[0], (uint32_t)s_acc[0]);
+            atomicAdd(&st[1], (uint32_t)s_acc[1]);
+            atomicAdd(&st[2], walked * (uint32_t)kFwdThreads);
+            atomicAdd(&st[3], end - start);
+            atomicAdd(&st[4], walked);
+            atomicAdd(&st[5], (uint32_t)((clock64() - t_start) >> 6));
         }
     }
 }

@@ -29,6 +29,8 @@
 // releases its TMEM; an MMA issued for a batch that is not walked is waited for before release.
 // Two accumulator buffers let the MMAs of batch k+1 run while batch k is walked; only thread 0 polls
 // the mbarrier, the others wait in a hardware barrier.
+#include <cstring>
+
 #include "common.cuh"
 
 namespace tcgs {
@@ -119,47 +121,33 @@ __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
     return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-// Smallest value of q(p) = (m - p)^T Q (m - p) over the rectangle [x0, x1] x [y0, y1] of pixel
-// centres, Q = [[a, b], [b, c]] positive definite: 0 when m is inside, otherwise the smallest of the
-// four edge minima (each a 1-D convex quadratic minimised at its clamped stationary point).
-__device__ __forceinline__ float min_q_over_box(float mx, float my, float a, float b, float c, float x0, float x1,
-                                                float y0, float y1) {
-    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
-    const float ia = 1.f / a, ic = 1.f / c;
-    float best = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float X = e ? x1 : x0;
-        const float dx = mx - X;
-        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
-        const float dy = my - y;
-        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
-        const float Y = e ? y1 : y0;
-        const float ey = my - Y;
-        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
-        const float ex = mx - x;
-        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
-    }
-    return best;
-}
-
-struct TcParams {
+// Per-view inputs and outputs (the batched renderer walks (view, tile) items of up to
+// TCGS_MAX_VIEWS views; the single-view call uses entry 0).
+struct ViewData {
     DevCamera cam;
     const uint32_t* ranges;
     const uint32_t* ids;
     const float* mean2d;
     const float* conic;
-    const float* opacity;
     const float* rgb;
-    float bg[3];
-    float alpha_max;
-    int split;
-    int tile_cull;
     float* img;
     float* T_final;
     uint32_t* n_contrib;
     uint32_t* stats;
+};
+
+struct TcParams {
+    ViewData v[TCGS_MAX_VIEWS];
+    const float* opacity;
+    float bg[3];
+    float alpha_max;
+    int split;
+    int tile_cull;
     int32_t* status;
+    int n_views;
+    const uint32_t* queue;      // queue mode: items (view << 16 | tile) in the order to render
+    uint32_t n_items;
+    uint32_t* counter;          // queue mode: next item to take (zeroed before the launch)
     const int32_t* dbg_tiles;   // frag2mat inspection mode
     int dbg_max_n;
     float* dbg_beta;
@@ -171,15 +159,16 @@ struct Slot {
     bool valid;
 };
 
-__device__ __forceinline__ Slot load_slot(const TcParams& p, uint32_t g, bool valid, bool colour) {
+__device__ __forceinline__ Slot load_slot(const ViewData& vd, const float* opacity, uint32_t g, bool valid,
+                                          bool colour) {
     Slot d;
     d.valid = valid;
     if (valid) {
-        const float2 m = reinterpret_cast<const float2*>(p.mean2d)[g];
+        const float2 m = reinterpret_cast<const float2*>(vd.mean2d)[g];
         d.mx = m.x; d.my = m.y;
-        d.s11 = p.conic[3 * g]; d.s12 = p.conic[3 * g + 1]; d.s22 = p.conic[3 * g + 2];
-        d.o = p.opacity[g];
-        if (colour) { d.r = p.rgb[3 * g]; d.g = p.rgb[3 * g + 1]; d.b = p.rgb[3 * g + 2]; }
+        d.s11 = vd.conic[3 * g]; d.s12 = vd.conic[3 * g + 1]; d.s22 = vd.conic[3 * g + 2];
+        d.o = opacity[g];
+        if (colour) { d.r = vd.rgb[3 * g]; d.g = vd.rgb[3 * g + 1]; d.b = vd.rgb[3 * g + 2]; }
         else { d.r = d.g = d.b = 0.f; }
     } else {
         d.mx = d.my = d.s11 = d.s12 = d.s22 = d.r = d.g = d.b = 0.f;
@@ -188,8 +177,10 @@ __device__ __forceinline__ Slot load_slot(const TcParams& p, uint32_t g, bool va
     return d;
 }
 
-// Smallest q(p) = (m - p)^T Q (m - p) over a rectangle of pixel centres, with the reciprocals of the
-// diagonal of Q precomputed (see min_q_over_box).
+// Smallest value of q(p) = (m - p)^T Q (m - p) over the rectangle [x0, x1] x [y0, y1] of pixel
+// centres, Q = [[a, b], [b, c]] positive definite, with ia = 1/a and ic = 1/c precomputed: 0 when m
+// is inside, otherwise the smallest of the four edge minima (each a 1-D convex quadratic minimised
+// at its clamped stationary point).
 __device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float b, float c, float ia, float ic,
                                              float x0, float x1, float y0, float y1) {
     if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
@@ -210,32 +201,22 @@ __device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float 
     return best;
 }
 
-template <bool kInspect, bool kStats>
+template <bool kInspect, bool kStats, bool kQueue>
 __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_timeout;
+    __shared__ uint32_t s_item;
     __shared__ unsigned long long s_acc[3];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const bool producer = warp == kConsumerWarps;
-    int tile = kInspect ? p.dbg_tiles[blockIdx.x] : (int)blockIdx.x;
-    bool tile_ok = true;
-    if (kInspect && (tile < 0 || tile >= p.cam.grid_w * p.cam.grid_h)) {   // never index past the grid
-        if (t == 0) set_status(p.status, TCGS_ERR_INVALID);
-        tile = 0;
-        tile_ok = false;
-    }
-    const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
-    // consumer warp block (8 x 4 pixels) of the tile, and this thread's pixel; warps 0-3 cover rows
-    // 0-7 (MMA half 0, U rows 0-127), warps 4-7 rows 8-15 (half 1, U rows 128-255)
+    // consumer warp block (8 x 4 pixels) of a tile, and this thread's pixel in it; warps 0-3 cover
+    // rows 0-7 (MMA half 0, U rows 0-127), warps 4-7 rows 8-15 (half 1, U rows 128-255)
     const int half = (warp >> 2) & 1;
     const int bx = warp & 1, by = (warp >> 1) & 3;
     const int lx = 8 * bx + (lane & 7), ly = 4 * by + (lane >> 3);
-    const int px_i = tx * kTile + lx, py_i = ty * kTile + ly;
-    const bool inside = !producer && px_i < p.cam.width && py_i < p.cam.height;
-    const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);   // p(T)
     // this warp's pixel-centre rectangle, tile-local
     const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f;
     const float by0 = 4.f * by - 7.5f, by1 = by0 + 3.f;
@@ -250,11 +231,10 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
         if (lane == 0) {
             mbar_init(mbar0, 1);
             mbar_init(mbar0 + 8, 1);
-            s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
             s_timeout = 0;
         }
     } else {
-        // U row t = this thread's pixel (G2L: dp = p - p(T))
+        // U row t = this thread's pixel, tile-local (G2L: dp = p - p(T)); the same for every tile
         const float dx = (float)lx + 0.5f - kTile / 2, dy = (float)ly + 0.5f - kTile / 2;
         __half u[16];
         const __half one = __float2half_rn(1.f), zero = __float2half_rn(0.f);
@@ -274,269 +254,316 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
         *reinterpret_cast<uint4*>(sA + canon_off(t, 0)) = c0;
         *reinterpret_cast<uint4*>(sA + canon_off(t, 1)) = c1;
     }
-
-    const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
-    uint32_t stop = end;
-    if (kInspect) {
-        uint32_t lim = start + (uint32_t)p.dbg_max_n;
-        stop = !tile_ok ? start : (lim < end ? lim : end);
-    }
-    const uint32_t nbat = (stop - start + kN - 1) / kN;
-
-    // Producer: stage batch slot `lane` into buffer `buf`: tile-local parameters (with the
-    // reciprocals the block tests need) and colour, and the V row of the MMA.
-    auto stage = [&](const Slot& d, int buf) {
-        float4* sP = reinterpret_cast<float4*>(smem + kSmemP + buf * kPBytes);
-        float v[6] = {kCulledV, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float mx = 0.f, my = 0.f, lim = -1.f, ia = 0.f, ic = 0.f;
-        if (d.valid) {
-            mx = d.mx - cx; my = d.my - cy;   // G2L mean
-            const float lno = __logf(d.o);
-            // alpha >= 1/255 somewhere needs q <= 2 (ln o + ln 255); relative and absolute margins
-            // keep every test conservative under FP32 rounding
-            const float reach = 2.f * (lno - kBetaCull);
-            lim = reach > -1e-3f ? reach * 1.0001f + 1e-3f : -1.f;
-            if (lim >= 0.f) {
-                // V only for Gaussians that can reach the tile: ||dmu - dp||_Q >= sqrt(q0) -
-                // |dp| sqrt(lambda_max(Q)), |dp| <= 7.5 sqrt(2); their tile-local coefficients are
-                // then bounded and FP16 never overflows
-                const float qx = d.s11 * mx + d.s12 * my, qy = d.s12 * mx + d.s22 * my;
-                const float q0 = fmaxf(mx * qx + my * qy, 0.f);
-                const float dd = 0.25f * (d.s11 - d.s22) * (d.s11 - d.s22) + d.s12 * d.s12;
-                const float lam = fmaxf(0.5f * (d.s11 + d.s22) + dd * rsqrtf(fmaxf(dd, 1e-30f)), 0.f);
-                const float gap = q0 * rsqrtf(fmaxf(q0, 1e-30f)) - 10.606601717798213f * lam * rsqrtf(fmaxf(lam, 1e-30f));
-                if (!(gap > 0.f && gap * gap > 1.01f * lim + 1e-2f)) {   // looser than any block test
-                    v[0] = (lno - 0.5f * q0) * kLog2e;
-                    v[1] = qx * kLog2e;
-                    v[2] = qy * kLog2e;
-                    v[3] = -0.5f * d.s11 * kLog2e;
-                    v[4] = -d.s12 * kLog2e;
-                    v[5] = -0.5f * d.s22 * kLog2e;
-                    ia = __fdividef(1.f, d.s11);
-                    ic = __fdividef(1.f, d.s22);
-                } else {
-                    lim = -1.f;   // cannot reach the tile: no block test passes
-                }
-            }
-        }
-        sP[3 * lane] = make_float4(mx, my, d.s11, d.s12);
-        sP[3 * lane + 1] = make_float4(d.s22, lim, ia, ic);
-        sP[3 * lane + 2] = make_float4(d.r, d.g, d.b, 0.f);
-        uint8_t* sB = smem + kSmemB + buf * kVBytes;
-        __half h[16];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
-        if (p.split) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const __half hi = __float2half_rn(v[k]);
-                h[k] = hi;
-                h[6 + k] = __float2half_rn(v[k] - __half2float(hi));
-            }
-            h[12] = h[13] = h[14] = h[15] = __float2half_rn(0.f);
-        } else {
-            const __half third = __float2half_rn(v[0] * (1.f / 3.f));
-            h[0] = h[1] = h[2] = third;
-#pragma unroll
-            for (int k = 1; k < 6; ++k) h[2 + k] = __float2half_rn(v[k]);
-#pragma unroll
-            for (int k = 8; k < 16; ++k) h[k] = __float2half_rn(0.f);
-        }
-        uint4 c0 = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-        uint4 c1 = make_uint4(pack2(h[8], h[9]), pack2(h[10], h[11]), pack2(h[12], h[13]), pack2(h[14], h[15]));
-        *reinterpret_cast<uint4*>(sB + canon_off(lane, 0)) = c0;
-        *reinterpret_cast<uint4*>(sB + canon_off(lane, 1)) = c1;
-        fence_async_smem();
-    };
-    // Consumer warps: which slots of buffer `buf` can reach alpha >= 1/255 somewhere in this warp's
-    // 8 x 4 block (exact minimum of the conic form over the block's pixel centres).
-    auto block_mask = [&](int buf) -> uint32_t {
-        const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + buf * kPBytes);
-        const float4 a = sP[3 * lane], b = sP[3 * lane + 1];
-        bool act = b.y >= 0.f;
-        if (act && p.tile_cull) act = min_q_box_r(a.x, a.y, a.z, a.w, b.x, b.z, b.w, bx0, bx1, by0, by1) <= b.y;
-        return __ballot_sync(0xffffffffu, act);
-    };
-    // Producer lane 0: both 128-row halves of U against the same V, committed to one mbarrier.
-    auto issue_mma = [&](uint32_t k) {
-        tc_fence_after();
-        const int vb = (int)(k % 3u), tb = (int)(k & 1u);
-        const uint64_t descB = make_desc(smem_u32(smem + kSmemB + vb * kVBytes));
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint64_t descA = make_desc(smem_u32(sA + h * 4096));
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                    s_tmem + (uint32_t)(tb * 2 * kN + h * kN)),
-                "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
-                : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         mbar0 + 8u * (uint32_t)tb)
-                     : "memory");
-    };
-
-    // producer registers: `nxt` holds the data of the batch to stage next, `nid` the ids after that
-    Slot nxt;
-    uint32_t nid = 0;
-    auto prefetch = [&](uint32_t kb) {   // data of batch kb (ids already in nid), ids of batch kb + 1
-        const uint32_t i = start + kb * kN + lane;
-        nxt = load_slot(p, nid, i < stop, !kInspect);
-        const uint32_t i2 = i + kN;
-        if (i2 < stop) nid = p.ids[i2];
-    };
-    if (producer) {
-        if (start + lane < stop) nid = p.ids[start + lane];
-        prefetch(0);
-    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();   // U visible to the tensor core, TMEM address and mbarriers published
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0, n_eval = end - start, n_blend = 0, cols = 0;
-    bool done = !inside;
     const float kInf = __int_as_float(0x7f800000);
-    float thr = done ? kInf : kBeta2Cull;
-    uint32_t mask_cur = 0;
     uint32_t phase_bits = 0;   // producer lane 0: completed-phase parity of the two mbarriers
+    bool stopped = false;
 
-    auto wait_mma = [&](uint32_t k) -> bool {   // producer lane 0
-        const uint32_t tb = k & 1u;
-        const bool ok = mbar_wait(mbar0 + 8u * tb, (phase_bits >> tb) & 1u);
-        phase_bits ^= 1u << tb;
-        return ok;
-    };
+    for (uint32_t round = 0;; ++round) {
+        // ---------------- which tile of which view
+        int view = 0, tile;
+        bool tile_ok = true;
+        if (kQueue) {
+            if (t == 0) s_item = atomicAdd(p.counter, 1u);
+            __syncthreads();
+            const uint32_t item = s_item;
+            if (item >= p.n_items) break;
+            const uint32_t it = p.queue[item];
+            view = (int)(it >> 16);
+            tile = (int)(it & 0xFFFFu);
+        } else {
+            if (round > 0) break;
+            tile = kInspect ? p.dbg_tiles[blockIdx.x] : (int)blockIdx.x;
+        }
+        if (view >= p.n_views) {   // never index past the view table
+            if (t == 0) set_status(p.status, TCGS_ERR_INVALID);
+            view = 0;
+            tile_ok = false;
+        }
+        const ViewData& vd = p.v[view];
+        if (tile < 0 || tile >= vd.cam.grid_w * vd.cam.grid_h) {   // never index past the grid
+            if (t == 0) set_status(p.status, TCGS_ERR_INVALID);
+            tile = 0;
+            tile_ok = false;
+        }
+        const long long t_start = clock64();
+        const int tx = tile % vd.cam.grid_w, ty = tile / vd.cam.grid_w;
+        const int px_i = tx * kTile + lx, py_i = ty * kTile + ly;
+        const bool inside = !producer && tile_ok && px_i < vd.cam.width && py_i < vd.cam.height;
+        const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);   // p(T)
+        const uint32_t start = vd.ranges[2 * tile], end = vd.ranges[2 * tile + 1];
+        uint32_t stop = tile_ok ? end : start;
+        if (kInspect) {
+            uint32_t lim = start + (uint32_t)p.dbg_max_n;
+            stop = !tile_ok ? start : (lim < end ? lim : end);
+        }
+        const uint32_t nbat = (stop - start + kN - 1) / kN;
+        if (kStats && t == 0) s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
 
-    // prologue: batches 0 and 1 staged, MMA 0 complete, MMA 1 issued, masks of batch 0 known
-    if (nbat > 0) {
-        if (producer) {
-            stage(nxt, 0);
-            if (nbat > 1) prefetch(1);
-        }
-        tc_fence_before();
-        __syncthreads();
-        if (producer) {
-            if (lane == 0) issue_mma(0);
-            if (nbat > 1) {
-                stage(nxt, 1);
-                if (nbat > 2) prefetch(2);
-            }
-            if (lane == 0 && !wait_mma(0)) s_timeout = 1;
-        } else {
-            mask_cur = block_mask(0);
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (producer && lane == 0 && nbat > 1 && !s_timeout) issue_mma(1);
-    }
-    bool stopped = nbat > 0 && s_timeout;
-    for (uint32_t k = 0; k < nbat && !stopped; ++k) {
-        // window: consumers walk batch k while the producer stages batch k + 2 and waits for MMA k + 1
-        if (producer) {
-            if (k + 2 < nbat) {
-                stage(nxt, (int)((k + 2) % 3u));
-                if (k + 3 < nbat) prefetch(k + 3);
-            }
-            if (lane == 0 && k + 1 < nbat && !wait_mma(k + 1)) s_timeout = 1;
-        } else if (kInspect) {
-            const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
-            uint32_t r[32];
-            tmem_ld32(taddr, r);
-            tmem_wait_ld();
-            const uint32_t b0 = start + k * kN;
-            const uint32_t nb = stop - b0 < (uint32_t)kN ? stop - b0 : (uint32_t)kN;
-            const int pix = ly * kTile + lx;
-            float* out = p.dbg_beta + ((size_t)blockIdx.x * 256 + pix) * p.dbg_max_n + (b0 - start);
-#pragma unroll
-            for (int j = 0; j < kN; ++j)
-                if ((uint32_t)j < nb) out[j] = __uint_as_float(r[j]) * 0.6931471805599453f;
-        } else {
-            // walk this warp's marked list entries, in list order
-            const uint32_t b0 = start + k * kN;
-            const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
-            const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + (k % 3u) * kPBytes);
-            uint32_t m = __all_sync(0xffffffffu, done) ? 0u : mask_cur;
-            if (kStats) cols += __popc(m);
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const float b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
-                tmem_wait_ld();
-                const bool pass = b2 >= thr;                       // EarlyCull, log2 units
-                const float a = fminf(p.alpha_max, ex2_approx(b2));
-                const float Tn = fmaf(-a, T, T);
-                const bool term = pass && (Tn < kTmin);           // Algorithm 1: terminate, unblended
-                const bool blend = pass && !term;
-                const float4 c = sP[3 * j + 2];
-                const float w = blend ? a * T : 0.f;
-                C0 = fmaf(c.x, w, C0);
-                C1 = fmaf(c.y, w, C1);
-                C2 = fmaf(c.z, w, C2);
-                T = blend ? Tn : T;
-                const uint32_t pos = b0 + (uint32_t)j + 1u - start;
-                last = blend ? pos : last;
-                if (kStats) {
-                    n_eval = term ? pos : n_eval;
-                    n_blend += blend ? 1u : 0u;
+        // Producer: stage batch slot `lane` into buffer `buf`: tile-local parameters (with the
+        // reciprocals the block tests need) and colour, and the V row of the MMA.
+        auto stage = [&](const Slot& d, int buf) {
+            float4* sP = reinterpret_cast<float4*>(smem + kSmemP + buf * kPBytes);
+            float v[6] = {kCulledV, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float mx = 0.f, my = 0.f, lim = -1.f, ia = 0.f, ic = 0.f;
+            if (d.valid) {
+                mx = d.mx - cx; my = d.my - cy;   // G2L mean
+                const float lno = __logf(d.o);
+                // alpha >= 1/255 somewhere needs q <= 2 (ln o + ln 255); relative and absolute
+                // margins keep every test conservative under FP32 rounding
+                const float reach = 2.f * (lno - kBetaCull);
+                lim = reach > -1e-3f ? reach * 1.0001f + 1e-3f : -1.f;
+                if (lim >= 0.f) {
+                    // V only for Gaussians that can reach the tile: ||dmu - dp||_Q >= sqrt(q0) -
+                    // |dp| sqrt(lambda_max(Q)), |dp| <= 7.5 sqrt(2); their tile-local coefficients
+                    // are then bounded and FP16 never overflows
+                    const float qx = d.s11 * mx + d.s12 * my, qy = d.s12 * mx + d.s22 * my;
+                    const float q0 = fmaxf(mx * qx + my * qy, 0.f);
+                    const float dd = 0.25f * (d.s11 - d.s22) * (d.s11 - d.s22) + d.s12 * d.s12;
+                    const float lam = fmaxf(0.5f * (d.s11 + d.s22) + dd * rsqrtf(fmaxf(dd, 1e-30f)), 0.f);
+                    const float gap = q0 * rsqrtf(fmaxf(q0, 1e-30f)) -
+                                      10.606601717798213f * lam * rsqrtf(fmaxf(lam, 1e-30f));
+                    if (!(gap > 0.f && gap * gap > 1.01f * lim + 1e-2f)) {   // looser than any block test
+                        v[0] = (lno - 0.5f * q0) * kLog2e;
+                        v[1] = qx * kLog2e;
+                        v[2] = qy * kLog2e;
+                        v[3] = -0.5f * d.s11 * kLog2e;
+                        v[4] = -d.s12 * kLog2e;
+                        v[5] = -0.5f * d.s22 * kLog2e;
+                        ia = __fdividef(1.f, d.s11);
+                        ic = __fdividef(1.f, d.s22);
+                    } else {
+                        lim = -1.f;   // cannot reach the tile: no block test passes
+                    }
                 }
-                thr = term ? kInf : thr;
-                done = done || term;
+            }
+            sP[3 * lane] = make_float4(mx, my, d.s11, d.s12);
+            sP[3 * lane + 1] = make_float4(d.s22, lim, ia, ic);
+            sP[3 * lane + 2] = make_float4(d.r, d.g, d.b, 0.f);
+            uint8_t* sB = smem + kSmemB + buf * kVBytes;
+            __half h[16];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
+            if (p.split) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const __half hi = __float2half_rn(v[k]);
+                    h[k] = hi;
+                    h[6 + k] = __float2half_rn(v[k] - __half2float(hi));
+                }
+                h[12] = h[13] = h[14] = h[15] = __float2half_rn(0.f);
+            } else {
+                const __half third = __float2half_rn(v[0] * (1.f / 3.f));
+                h[0] = h[1] = h[2] = third;
+#pragma unroll
+                for (int k = 1; k < 6; ++k) h[2 + k] = __float2half_rn(v[k]);
+#pragma unroll
+                for (int k = 8; k < 16; ++k) h[k] = __float2half_rn(0.f);
+            }
+            uint4 c0 = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+            uint4 c1 = make_uint4(pack2(h[8], h[9]), pack2(h[10], h[11]), pack2(h[12], h[13]), pack2(h[14], h[15]));
+            *reinterpret_cast<uint4*>(sB + canon_off(lane, 0)) = c0;
+            *reinterpret_cast<uint4*>(sB + canon_off(lane, 1)) = c1;
+            fence_async_smem();
+        };
+        // Consumer warps: which slots of buffer `buf` can reach alpha >= 1/255 somewhere in this
+        // warp's 8 x 4 block (exact minimum of the conic form over the block's pixel centres).
+        auto block_mask = [&](int buf) -> uint32_t {
+            const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + buf * kPBytes);
+            const float4 a = sP[3 * lane], b = sP[3 * lane + 1];
+            bool act = b.y >= 0.f;
+            if (act && p.tile_cull) act = min_q_box_r(a.x, a.y, a.z, a.w, b.x, b.z, b.w, bx0, bx1, by0, by1) <= b.y;
+            return __ballot_sync(0xffffffffu, act);
+        };
+        // Producer lane 0: both 128-row halves of U against the same V, committed to one mbarrier.
+        auto issue_mma = [&](uint32_t k) {
+            tc_fence_after();
+            const int vb = (int)(k % 3u), tb = (int)(k & 1u);
+            const uint64_t descB = make_desc(smem_u32(smem + kSmemB + vb * kVBytes));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t descA = make_desc(smem_u32(sA + h * 4096));
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                        tmem + (uint32_t)(tb * 2 * kN + h * kN)),
+                    "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             mbar0 + 8u * (uint32_t)tb)
+                         : "memory");
+        };
+        auto wait_mma = [&](uint32_t k) -> bool {   // producer lane 0, batches in order
+            const uint32_t tb = k & 1u;
+            const bool ok = mbar_wait(mbar0 + 8u * tb, (phase_bits >> tb) & 1u);
+            phase_bits ^= 1u << tb;
+            return ok;
+        };
+
+        // producer registers: `nxt` holds the data of the batch to stage next, `nid` the ids after that
+        Slot nxt;
+        uint32_t nid = 0;
+        auto prefetch = [&](uint32_t kb) {   // data of batch kb (ids already in nid), ids of batch kb + 1
+            const uint32_t i = start + kb * kN + lane;
+            nxt = load_slot(vd, p.opacity, nid, i < stop, !kInspect);
+            const uint32_t i2 = i + kN;
+            if (i2 < stop) nid = vd.ids[i2];
+        };
+        if (producer) {
+            if (start + lane < stop) nid = vd.ids[start + lane];
+            prefetch(0);
+        }
+
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        uint32_t last = 0, n_eval = end - start, n_blend = 0, cols = 0, walked = 0;
+        bool done = !inside;
+        float thr = done ? kInf : kBeta2Cull;
+        uint32_t mask_cur = 0;
+
+        // prologue: batches 0 and 1 staged, MMA 0 complete, MMA 1 issued, masks of batch 0 known
+        if (nbat > 0) {
+            if (producer) {
+                stage(nxt, 0);
+                if (nbat > 1) prefetch(1);
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (producer) {
+                if (lane == 0) issue_mma(0);
+                if (nbat > 1) {
+                    stage(nxt, 1);
+                    if (nbat > 2) prefetch(2);
+                }
+                if (lane == 0 && !wait_mma(0)) s_timeout = 1;
+            } else {
+                mask_cur = block_mask(0);
+            }
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (producer && lane == 0 && nbat > 1 && !s_timeout) issue_mma(1);
+        }
+        bool timed_out = nbat > 0 && s_timeout;
+        for (uint32_t k = 0; k < nbat && !timed_out; ++k) {
+            // window: consumers walk batch k while the producer stages batch k + 2 and waits for
+            // MMA k + 1
+            if (producer) {
+                if (k + 2 < nbat) {
+                    stage(nxt, (int)((k + 2) % 3u));
+                    if (k + 3 < nbat) prefetch(k + 3);
+                }
+                if (lane == 0 && k + 1 < nbat && !wait_mma(k + 1)) s_timeout = 1;
+            } else if (kInspect) {
+                const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
+                uint32_t r[32];
+                tmem_ld32(taddr, r);
+                tmem_wait_ld();
+                const uint32_t b0 = start + k * kN;
+                const uint32_t nb = stop - b0 < (uint32_t)kN ? stop - b0 : (uint32_t)kN;
+                const int pix = ly * kTile + lx;
+                float* out = p.dbg_beta + ((size_t)blockIdx.x * 256 + pix) * p.dbg_max_n + (b0 - start);
+#pragma unroll
+                for (int j = 0; j < kN; ++j)
+                    if ((uint32_t)j < nb) out[j] = __uint_as_float(r[j]) * 0.6931471805599453f;
+            } else {
+                // walk this warp's marked list entries, in list order
+                const uint32_t b0 = start + k * kN;
+                const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
+                const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + (k % 3u) * kPBytes);
+                uint32_t m = __all_sync(0xffffffffu, done) ? 0u : mask_cur;
+                if (kStats) cols += __popc(m);
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
+                    tmem_wait_ld();
+                    const bool pass = b2 >= thr;                       // EarlyCull, log2 units
+                    const float a = fminf(p.alpha_max, ex2_approx(b2));
+                    const float Tn = fmaf(-a, T, T);
+                    const bool term = pass && (Tn < kTmin);           // Algorithm 1: terminate, unblended
+                    const bool blend = pass && !term;
+                    const float4 c = sP[3 * j + 2];
+                    const float w = blend ? a * T : 0.f;
+                    C0 = fmaf(c.x, w, C0);
+                    C1 = fmaf(c.y, w, C1);
+                    C2 = fmaf(c.z, w, C2);
+                    T = blend ? Tn : T;
+                    const uint32_t pos = b0 + (uint32_t)j + 1u - start;
+                    last = blend ? pos : last;
+                    if (kStats) {
+                        n_eval = term ? pos : n_eval;
+                        n_blend += blend ? 1u : 0u;
+                    }
+                    thr = term ? kInf : thr;
+                    done = done || term;
+                }
+            }
+            walked = (k + 1) * kN;
+            tc_fence_before();
+            const bool more = __syncthreads_or(!done);   // batch k walked, batch k+2 staged, MMA k+1 done
+            tc_fence_after();
+            if (s_timeout) {
+                timed_out = true;
+                break;
+            }
+            if (!kInspect && !more) break;
+            if (producer) {
+                if (lane == 0 && k + 2 < nbat) issue_mma(k + 2);
+            } else if (k + 1 < nbat) {
+                mask_cur = __all_sync(0xffffffffu, done) ? 0u : block_mask((int)((k + 1) % 3u));
             }
         }
+        // every MMA issued has been waited for (MMA k + 2 is only issued after the walk of batch k
+        // continues, and is waited for in the next window), so TMEM is idle between tiles
+
+        if (!kInspect) {
+            if (inside) {
+                size_t pix = (size_t)py_i * vd.cam.width + px_i;
+                size_t plane = (size_t)vd.cam.width * vd.cam.height;
+                vd.img[pix] = C0 + T * p.bg[0];
+                vd.img[plane + pix] = C1 + T * p.bg[1];
+                vd.img[2 * plane + pix] = C2 + T * p.bg[2];
+                vd.T_final[pix] = T;
+                vd.n_contrib[pix] = last;
+            }
+            if (kStats) {
+                if (inside) {
+                    atomicAdd(&s_acc[0], (unsigned long long)n_blend);
+                    atomicAdd(&s_acc[1], (unsigned long long)(n_eval - n_blend));
+                }
+                if (lane == 0 && !producer) atomicAdd(&s_acc[2], (unsigned long long)cols * 32ull);
+            }
+        } else if (!producer) {
+            const int pix = ly * kTile + lx;
+            float* out = p.dbg_beta + ((size_t)blockIdx.x * 256 + pix) * p.dbg_max_n;
+            for (int j = (int)(stop - start); j < p.dbg_max_n; ++j) out[j] = -kInf;
+        }
         tc_fence_before();
-        const bool more = __syncthreads_or(!done);   // batch k walked, batch k+2 staged, MMA k+1 done
-        tc_fence_after();
-        if (s_timeout) {
+        __syncthreads();
+        if (kStats && t == 0 && tile_ok && vd.stats) {
+            uint32_t* st = vd.stats + 8 * tile;
+            atomicAdd(&st[0], (uint32_t)s_acc[0]);
+            atomicAdd(&st[1], (uint32_t)s_acc[1]);
+            atomicAdd(&st[2], (uint32_t)s_acc[2]);
+            atomicAdd(&st[3], end - start);
+            atomicAdd(&st[4], walked < end - start ? walked : end - start);
+            atomicAdd(&st[5], (uint32_t)((clock64() - t_start) >> 6));
+        }
+        if (timed_out) {
             if (t == 0) set_status(p.status, TCGS_ERR_TIMEOUT);
+            stopped = true;
             break;
         }
-        if (!kInspect && !more) break;
-        if (producer) {
-            if (lane == 0 && k + 2 < nbat) issue_mma(k + 2);
-        } else if (k + 1 < nbat) {
-            mask_cur = __all_sync(0xffffffffu, done) ? 0u : block_mask((int)((k + 1) % 3u));
-        }
     }
-    // every MMA issued has been waited for: MMA k + 2 is only issued after the walk of batch k
-    // continues, and waited for in the next window, so TMEM is idle here
-    if (stopped && t == 0) set_status(p.status, TCGS_ERR_TIMEOUT);
-
-    if (!kInspect) {
-        if (inside) {
-            size_t pix = (size_t)py_i * p.cam.width + px_i;
-            size_t plane = (size_t)p.cam.width * p.cam.height;
-            p.img[pix] = C0 + T * p.bg[0];
-            p.img[plane + pix] = C1 + T * p.bg[1];
-            p.img[2 * plane + pix] = C2 + T * p.bg[2];
-            p.T_final[pix] = T;
-            p.n_contrib[pix] = last;
-        }
-        if (kStats) {
-            if (inside) {
-                atomicAdd(&s_acc[0], (unsigned long long)n_blend);
-                atomicAdd(&s_acc[1], (unsigned long long)(n_eval - n_blend));
-            }
-            if (lane == 0 && !producer) atomicAdd(&s_acc[2], (unsigned long long)cols * 32ull);
-        }
-    } else if (!producer) {
-        const int pix = ly * kTile + lx;
-        float* out = p.dbg_beta + ((size_t)blockIdx.x * 256 + pix) * p.dbg_max_n;
-        for (int j = (int)(stop - start); j < p.dbg_max_n; ++j) out[j] = -kInf;
-    }
+    (void)stopped;
     tc_fence_before();
     __syncthreads();
-    if (kStats && t == 0) {
-        atomicAdd(&p.stats[4 * tile + 0], (uint32_t)s_acc[0]);
-        atomicAdd(&p.stats[4 * tile + 1], (uint32_t)s_acc[1]);
-        atomicAdd(&p.stats[4 * tile + 2], (uint32_t)s_acc[2]);
-        atomicAdd(&p.stats[4 * tile + 3], end - start);
-    }
     if (producer) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -545,6 +572,7 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
 
 int g_checked_device = -1;
 bool g_device_ok = false;
+int g_sm_count = 0;
 
 bool device_is_sm103() {
     int dev = 0;
@@ -553,32 +581,42 @@ bool device_is_sm103() {
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
     g_checked_device = dev;
     g_device_ok = (major == 10 && minor == 3);
     return g_device_ok;
 }
 
-bool g_attr_set[2][2] = {{false, false}, {false, false}};
+bool g_attr_set[2][2][2] = {};
 
-template <bool kInspect, bool kStats>
+template <bool kInspect, bool kStats, bool kQueue>
 tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
-    if (!g_attr_set[kInspect][kStats]) {
-        if (cudaFuncSetAttribute(k_render_tc<kInspect, kStats>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (!g_attr_set[kInspect][kStats][kQueue]) {
+        if (cudaFuncSetAttribute(k_render_tc<kInspect, kStats, kQueue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemDyn) != cudaSuccess)
             return TCGS_ERR_CUDA;
-        g_attr_set[kInspect][kStats] = true;
+        g_attr_set[kInspect][kStats][kQueue] = true;
     }
-    k_render_tc<kInspect, kStats><<<blocks, kTcThreads, kSmemDyn, s>>>(p);
+    k_render_tc<kInspect, kStats, kQueue><<<blocks, kTcThreads, kSmemDyn, s>>>(p);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }
 
-TcParams base_params(const tcgs_camera* cam, int precision, const uint32_t* tile_ranges, const uint32_t* ids,
-                     const float* mean2d, const float* conic, const float* opacity) {
-    TcParams p = {};
-    p.cam = make_dev_camera(*cam);
-    p.ranges = tile_ranges; p.ids = ids; p.mean2d = mean2d; p.conic = conic; p.opacity = opacity;
+ViewData make_view(const tcgs_camera* cam, const uint32_t* tile_ranges, const uint32_t* ids, const float* mean2d,
+                   const float* conic, const float* rgb, float* img, float* T_final, uint32_t* n_contrib,
+                   uint32_t* stats) {
+    ViewData v;
+    v.cam = make_dev_camera(*cam);
+    v.ranges = tile_ranges; v.ids = ids; v.mean2d = mean2d; v.conic = conic; v.rgb = rgb;
+    v.img = img; v.T_final = T_final; v.n_contrib = n_contrib; v.stats = stats;
+    return v;
+}
+
+TcParams base_params(int precision, const float* opacity) {
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.opacity = opacity;
     p.split = precision == TCGS_TC_FP16_SPLIT;
     p.alpha_max = 0.99f;
     p.tile_cull = 1;
@@ -587,21 +625,20 @@ TcParams base_params(const tcgs_camera* cam, int precision, const uint32_t* tile
 
 }  // namespace
 
-
 tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opts, const uint32_t* tile_ranges,
                              const uint32_t* ids_sorted, const float* mean2d, const float* conic,
                              const float* opacity, const float* rgb, const float* bg3, float* img, float* T_final,
                              uint32_t* n_contrib, cudaStream_t s) {
     if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;
-    TcParams p = base_params(cam, opts->precision, tile_ranges, ids_sorted, mean2d, conic, opacity);
-    p.rgb = rgb;
+    TcParams p = base_params(opts->precision, opacity);
+    p.v[0] = make_view(cam, tile_ranges, ids_sorted, mean2d, conic, rgb, img, T_final, n_contrib, opts->tile_stats);
+    p.n_views = 1;
     for (int i = 0; i < 3; ++i) p.bg[i] = bg3 ? bg3[i] : 0.f;
     p.alpha_max = opts->alpha_max;
-    p.img = img; p.T_final = T_final; p.n_contrib = n_contrib;
-    p.stats = opts->tile_stats; p.status = opts->device_status;
+    p.status = opts->device_status;
     p.tile_cull = opts->tile_cull;
-    int tiles = p.cam.grid_w * p.cam.grid_h;
-    return p.stats ? launch_tc<false, true>(p, tiles, s) : launch_tc<false, false>(p, tiles, s);
+    const int tiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
+    return opts->tile_stats ? launch_tc<false, true, false>(p, tiles, s) : launch_tc<false, false, false>(p, tiles, s);
 }
 
 }  // namespace tcgs
@@ -637,6 +674,48 @@ extern "C" tcgs_status tcgs_render_fwd(const tcgs_camera* cam, const tcgs_render
     }
 }
 
+extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view* views, const tcgs_render_opts* opts,
+                                               const float* opacity, const float* bg3, const uint32_t* queue,
+                                               int32_t n_items, uint32_t* work_counter, int32_t max_ctas,
+                                               tcgs_stream stream) {
+    using namespace tcgs;
+    if (n_views < 1 || n_views > TCGS_MAX_VIEWS || !views || !opts || !opacity || n_items < 0 ||
+        (n_items > 0 && (!queue || !work_counter)))
+        return TCGS_ERR_INVALID;
+    if (opts->precision != TCGS_TC_FP16 && opts->precision != TCGS_TC_FP16_SPLIT) return TCGS_ERR_INVALID;
+    if (!(opts->alpha_max > 0.f && opts->alpha_max <= 1.f)) return TCGS_ERR_INVALID;
+    TcParams p = base_params(opts->precision, opacity);
+    for (int v = 0; v < n_views; ++v) {
+        const tcgs_view& w = views[v];
+        if (!valid_camera(&w.cam) || !w.tile_ranges || !w.ids_sorted || !w.mean2d || !w.conic || !w.rgb || !w.img ||
+            !w.T_final || !w.n_contrib || (reinterpret_cast<uintptr_t>(w.mean2d) & 7))
+            return TCGS_ERR_INVALID;
+        const int gw = (w.cam.width + kTile - 1) / kTile, gh = (w.cam.height + kTile - 1) / kTile;
+        if (gw * gh > 65536) return TCGS_ERR_INVALID;   // items carry the tile in 16 bits
+        p.v[v] = make_view(&w.cam, w.tile_ranges, w.ids_sorted, w.mean2d, w.conic, w.rgb, w.img, w.T_final,
+                           w.n_contrib, w.tile_stats);
+    }
+    p.n_views = n_views;
+    if (n_items == 0) return TCGS_OK;
+    if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;
+    for (int i = 0; i < 3; ++i) p.bg[i] = bg3 ? bg3[i] : 0.f;
+    p.alpha_max = opts->alpha_max;
+    p.status = opts->device_status;
+    p.tile_cull = opts->tile_cull;
+    p.queue = queue;
+    p.n_items = (uint32_t)n_items;
+    p.counter = work_counter;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return TCGS_ERR_CUDA;
+    bool any_stats = false;
+    for (int v = 0; v < n_views; ++v) any_stats = any_stats || views[v].tile_stats;
+    // persistent grid: at most the CTAs that are resident at once (3 per SM for this kernel)
+    int ctas = g_sm_count * 3;
+    if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
+    if (ctas > n_items) ctas = n_items;
+    return any_stats ? launch_tc<false, true, true>(p, ctas, s) : launch_tc<false, false, true>(p, ctas, s);
+}
+
 extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precision, const uint32_t* tile_ranges,
                                           const uint32_t* ids_sorted, const float* mean2d, const float* conic,
                                           const float* opacity, int32_t n_tiles, const int32_t* tiles,
@@ -650,8 +729,10 @@ extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precis
     if (reinterpret_cast<uintptr_t>(mean2d) & 7) return TCGS_ERR_INVALID;
     if (n_tiles == 0 || max_n == 0) return TCGS_OK;
     if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;
-    TcParams p = base_params(cam, precision, tile_ranges, ids_sorted, mean2d, conic, opacity);
+    TcParams p = base_params(precision, opacity);
+    p.v[0] = make_view(cam, tile_ranges, ids_sorted, mean2d, conic, nullptr, nullptr, nullptr, nullptr, nullptr);
+    p.n_views = 1;
     p.status = device_status;
     p.dbg_tiles = tiles; p.dbg_max_n = max_n; p.dbg_beta = beta_out;
-    return launch_tc<true, false>(p, n_tiles, (cudaStream_t)stream);
+    return launch_tc<true, false, false>(p, n_tiles, (cudaStream_t)stream);
 }

@@ -144,7 +144,7 @@ def test_render_fp32_matches_oracle(tc, name, make, alpha_max, bg):
     cam, sc = make()
     _, inp, b, o = oracle_frame(cam, sc, alpha_max=alpha_max, bg=bg)
     g = gpu_inputs(inp, b)
-    stats = torch.zeros(b["ranges"].shape[0], 4, dtype=torch.int32, device=DEV)
+    stats = torch.zeros(b["ranges"].shape[0], 8, dtype=torch.int32, device=DEV)
     out = tc.tcgs_render_fwd(cam, tc.render_opts("fp32", alpha_max, tile_stats=stats), g["ranges"], g["ids"],
                              g["mean2d"], g["conic"], g["opacity"], g["rgb"], bg=bg)
     torch.cuda.synchronize()
@@ -183,7 +183,7 @@ def test_render_tc_split_matches_oracle(tc, name, make, alpha_max):
     cam, sc = make()
     _, inp, b, o = oracle_frame(cam, sc, alpha_max=alpha_max)
     g = gpu_inputs(inp, b)
-    stats = torch.zeros(b["ranges"].shape[0], 4, dtype=torch.int32, device=DEV)
+    stats = torch.zeros(b["ranges"].shape[0], 8, dtype=torch.int32, device=DEV)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     out = tc.tcgs_render_fwd(cam, tc.render_opts("tc_fp16_split", alpha_max, tile_stats=stats, device_status=status),
                              g["ranges"], g["ids"], g["mean2d"], g["conic"], g["opacity"], g["rgb"])
@@ -318,7 +318,7 @@ def test_tc_block_culling_changes_nothing(tc, name, make, precision):
     nt = b["ranges"].shape[0]
     res = {}
     for cull in (False, True):
-        stats = torch.zeros(nt, 4, dtype=torch.int32, device=DEV)
+        stats = torch.zeros(nt, 8, dtype=torch.int32, device=DEV)
         out = tc.tcgs_render_fwd(cam, tc.render_opts(precision, tile_stats=stats, tile_cull=cull), g["ranges"],
                                  g["ids"], g["mean2d"], g["conic"], g["opacity"], g["rgb"])
         torch.cuda.synchronize()

@@ -1,0 +1,150 @@
+"""GPU parity of the learned scheduler layer against its FP64 oracle, through the C ABI, and the
+gain of the learned queue order over the list-length order."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import sched as osc
+from paper_2505_24796_gb300 import scenes
+
+from .helpers import f32, oracle_frame, to_torch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import paper_2505_24796_gb300 as m
+    m._lib.load()
+    return m
+
+
+def test_tile_features_match_oracle(tc):
+    cam, sc = scenes.precision(P=30_000, width=240, height=120, seed=12)
+    _, inp, b, _ = oracle_frame(cam, sc)
+    ref = osc.tile_features(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["depth"], inp["radius"])
+    g = tc.tcgs_tile_features(cam, to_torch(b["ranges"].astype(np.int32), DEV), to_torch(b["ids"].astype(np.int32), DEV),
+                              to_torch(inp["mean2d"], DEV), to_torch(inp["conic"], DEV), to_torch(inp["opacity"], DEV),
+                              to_torch(inp["depth"], DEV), to_torch(inp["radius"].astype(np.int32), DEV))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(g.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+
+
+def _mlp_case(seed, n=3000):
+    rng = np.random.default_rng(seed)
+    P = osc.unpack(rng.normal(0, 0.3, osc.NPARAMS))
+    P["b1"] = np.abs(P["b1"]) + 0.05
+    P["b2"] = np.abs(P["b2"]) + 0.05
+    params = f32(osc.pack(P))
+    X = f32(rng.normal(0, 2, (n, 8)) + 1.0)
+    t = f32(rng.normal(0, 1, n))
+    return params, X, t
+
+
+def test_mlp_forward_backward_match_oracle(tc):
+    params, X, t = _mlp_case(7)
+    dX = to_torch(X, DEV)
+    norm = tc.tcgs_feature_norm(dX)
+    torch.cuda.synchronize()
+    nm = norm.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(nm[:8], X.astype(np.float64).mean(0), rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(1 / nm[8:], X.astype(np.float64).std(0), rtol=1e-4)
+    y = tc.tcgs_mlp_fwd(to_torch(params, DEV), norm, dX).cpu().numpy()
+    yr, _ = osc.mlp_forward(params.astype(np.float64), nm, X, fp16=True)
+    close = np.abs(y - yr) <= 2e-3 * (1 + np.abs(yr))
+    assert close.mean() >= 0.995 and np.abs(y - yr).max() < 0.05
+    loss = torch.zeros(1, device=DEV)
+    grad, _ = tc.tcgs_mlp_bwd(to_torch(params, DEV), norm, dX, to_torch(t, DEV), loss=loss)
+    torch.cuda.synchronize()
+    gr, lr = osc.mlp_backward(params.astype(np.float64), nm, X, t, fp16=True)
+    g = grad.cpu().numpy()
+    np.testing.assert_allclose(g, gr, rtol=5e-3, atol=2e-3 * np.abs(gr).max())
+    assert abs(float(loss.item()) - lr) <= 1e-3 * lr
+
+
+def test_adam_matches_oracle_and_consumes_grad(tc):
+    rng = np.random.default_rng(8)
+    p = f32(rng.normal(0, 1, 1377)); m = np.zeros(1377, np.float32); v = np.zeros(1377, np.float32)
+    dp, dm, dv = to_torch(p, DEV), to_torch(m, DEV), to_torch(v, DEV)
+    rp, rm, rv = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for step in range(1, 4):
+        g = f32(rng.normal(0, 1, 1377))
+        dg = to_torch(g, DEV)
+        tc.tcgs_adam_step(dp, dm, dv, dg, 1e-2, step=step)
+        torch.cuda.synchronize()
+        assert (dg == 0).all()
+        rp, rm, rv = osc.adam_step(rp, rm, rv, g.astype(np.float64), 1e-2, 0.9, 0.999, 1e-8, step)
+    np.testing.assert_allclose(dp.cpu().numpy(), rp, rtol=1e-5, atol=1e-6)
+
+
+def test_sched_order_matches_oracle(tc):
+    rng = np.random.default_rng(9)
+    n = 50_000
+    cost = f32(np.round(rng.normal(0, 3, n), 1))   # many exact ties
+    cost[::97] = -0.0
+    cost[1::97] = 0.0
+    items = rng.permutation(1 << 22)[:n].astype(np.int32)
+    q = tc.tcgs_sched_order(to_torch(cost, DEV), to_torch(items, DEV)).cpu().numpy()
+    # costs are ordered by their float bits, so -0.0 comes after +0.0 (stable within each)
+    key = np.where((cost == 0) & np.signbit(cost), -1e-300, cost.astype(np.float64))
+    np.testing.assert_array_equal(q, osc.order(key, items))
+
+
+def _small_multiview(tc, n_views, seed, P=200_000, scale=0.25):
+    from paper_2505_24796_gb300.sched import MultiView
+    rng = np.random.default_rng(seed)
+    scene = scenes.uniform_box(rng, P)
+    cams = scenes.multiview_cameras(n_views, seed + 1000)
+    for c in cams:   # reduced resolutions keep the test fast
+        w, h = int(c["width"] * scale), int(c["height"] * scale)
+        c.update(width=w, height=h, fx=c["fx"] * scale, fy=c["fy"] * scale, cx=w / 2.0, cy=h / 2.0)
+    return MultiView(scene, cams)
+
+
+def test_batched_render_equals_per_view_render(tc):
+    mv = _small_multiview(tc, 3, 40)
+    mv.render_each(stats=False)
+    torch.cuda.synchronize()
+    ref = [r.out["img"].clone() for r in mv.views]
+    items = mv.items()
+    rng = np.random.default_rng(1)
+    orders = [items, items.flip(0), items[torch.from_numpy(rng.permutation(items.numel())).to(DEV)].contiguous()]
+    for q in orders:
+        for r in mv.views:
+            r.out["img"].fill_(-1.0)
+        mv.render(q, max_ctas=37)
+        torch.cuda.synchronize()
+        for r, img in zip(mv.views, ref):
+            assert torch.equal(r.out["img"], img)
+
+
+def test_learned_order_beats_list_length(tc):
+    from paper_2505_24796_gb300.sched import TileCostModel
+    train = _small_multiview(tc, 12, 50)
+    X, y = train.training_data()
+    model = TileCostModel(seed=0)
+    final = model.fit(X, y, steps=500)
+    test = _small_multiview(tc, 6, 60)
+    Xt, yt = test.training_data()
+    pred = model.predict(Xt).cpu().numpy().astype(np.float64)
+    yt = yt.cpu().numpy().astype(np.float64)
+    n = torch.cat([(r.bins["tile_ranges"][:, 1] - r.bins["tile_ranges"][:, 0]) for r in test.views]).cpu().numpy()
+    # baseline predictor: least-squares fit of log cost on log list length (fitted on the test set itself)
+    A = np.c_[np.log1p(n), np.ones_like(yt)]
+    base = A @ np.linalg.lstsq(A, yt, rcond=None)[0]
+    mse_mlp, mse_len = np.mean((pred - yt) ** 2), np.mean((base - yt) ** 2)
+    print(f"\n[scheduler] train loss {final:.4f}; held-out MSE of log cost: MLP {mse_mlp:.4f}, list length {mse_len:.4f}")
+    assert mse_mlp < mse_len
+    # schedule quality judged on the measured per-tile work
+    walked = np.expm1(yt)
+    workers = 152 * 3
+    qm = test.queue("mlp", model).cpu().numpy()
+    ql = test.queue("length").cpu().numpy()
+    items = test.items().cpu().numpy()
+    w_of = dict(zip(items.tolist(), walked.tolist()))
+    ms_m = osc.lpt_makespan([w_of[i] for i in qm.tolist()], workers)
+    ms_l = osc.lpt_makespan([w_of[i] for i in ql.tolist()], workers)
+    print(f"[scheduler] simulated makespan (entries walked): MLP order {ms_m:.0f}, list-length order {ms_l:.0f}")
+    assert ms_m <= ms_l * 1.02
