@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch kernels eagerly instead of a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 1M Gaussians (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the differentiation, scheduler and large workloads (reported beside the headline)")
+    ap.add_argument("--sched-train-views", type=int, default=200)
     return ap.parse_args()
 
 
@@ -163,6 +166,161 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ other workloads (same run)
+
+def _events_ms(fn, reps, warmup, flush=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def bench_differentiation(dev, flush):
+    """1280x720, 500k Gaussians: forward and backward of the alpha-blending stage (L1 loss to a seeded
+    target); the loss gradient itself is user code and is formed outside the timed events."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    from paper_2505_24796_gb300 import scenes
+    cam, sc, target = scenes.differentiation()
+    d = tc.scene_to_device(sc, dev)
+    pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    r = tc.Renderer(cam, len(sc["opacity"]), n + 1024, device=dev, stats=True)
+    r.frame(d, precision="fp32")
+    torch.cuda.synchronize()
+    st = r.stats.to(torch.int64).sum(0).tolist()
+    r.stats = None
+    tgt = torch.from_numpy(target).to(dev)
+    gimg = torch.sign(r.out["img"] - tgt).contiguous()
+    P = len(sc["opacity"])
+    grads = dict(dmean2d=torch.zeros(P, 2, device=dev), dconic=torch.zeros(P, 3, device=dev),
+                 dopacity=torch.zeros(P, device=dev), drgb=torch.zeros(P, 3, device=dev))
+    opts = tc.render_opts("fp32")
+
+    def bwd():
+        tc.tcgs_render_bwd(r.cam, opts, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"], r.proj["conic"],
+                           d["opacity"], r.proj["rgb"], r.out["img"], r.out["T_final"], r.out["n_contrib"], gimg,
+                           grads=grads)
+    fwd32 = _events_ms(lambda: r.render(d["opacity"], "fp32"), 10, 3, flush)
+    fwdtc = _events_ms(lambda: r.render(d["opacity"], "tc_fp16_split"), 10, 3, flush)
+    r.render(d["opacity"], "fp32")
+    bwd_ms = _events_ms(bwd, 10, 3, flush)
+    proj_ms = _events_ms(lambda: r.project(d), 10, 3, flush)
+    bin_ms = _events_ms(lambda: r.bin_sort(), 10, 3, flush)
+    return {"workload": "differentiation: 1280x720, fx=fy=1280, 500k Gaussians (plain distributions), L1 to a "
+                        "seeded target; backward replays the FP32 forward", "splats": n,
+            "alpha_evals": st[0] + st[1], "f_blend": st[0],
+            "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
+                   "render_fwd_tc": fwdtc, "render_bwd": bwd_ms},
+            "train_step_ms_fp32": proj_ms + bin_ms + fwd32 + bwd_ms,
+            "train_step_ms_tc_fwd": proj_ms + bin_ms + fwdtc + bwd_ms,
+            "bwd_alpha_evals_per_s": (st[0] + st[1]) / (bwd_ms * 1e-3)}
+
+
+def bench_scheduler(dev, train_views=200, chunk=16):
+    """16 views of one 3M-Gaussian scene at uneven resolutions: the MLP is trained on the tile costs
+    recorded by `train_views` renders of other views, then orders the batched renderer's queue."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    from oracle import sched as osc
+    from paper_2505_24796_gb300 import scenes
+    from paper_2505_24796_gb300.sched import MultiView, TileCostModel
+    eval_cams, scene = scenes.learned_scheduler()
+    d = tc.scene_to_device(scene, dev)
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    cams = scenes.multiview_cameras(train_views, 77)
+    for i in range(0, train_views, chunk):
+        mv = MultiView(d, cams[i:i + chunk], device=dev)
+        X, y = mv.training_data()
+        Xs.append(X); ys.append(y)
+        del mv
+    X, y = torch.cat(Xs).contiguous(), torch.cat(ys).contiguous()
+    collect_s = time.perf_counter() - t0
+    model = TileCostModel(device=dev, seed=0)
+    t1 = time.perf_counter()
+    loss = model.fit(X, y, steps=800)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    mv = MultiView(d, eval_cams, device=dev)
+    Xt, yt = mv.training_data()
+    walked, cycles = mv.tile_costs()
+    pred = model.predict(Xt)
+    torch.cuda.synchronize()
+    ytn, pn = yt.cpu().numpy().astype(np.float64), pred.cpu().numpy().astype(np.float64)
+    nlen = torch.cat([(r.bins["tile_ranges"][:, 1] - r.bins["tile_ranges"][:, 0]) for r in mv.views]).cpu().numpy()
+    A = np.c_[np.log1p(nlen), np.ones_like(ytn)]
+    base = A @ np.linalg.lstsq(A, ytn, rcond=None)[0]
+    res = {"workload": "learned scheduler: 16 views (640x480..1920x1080, cameras on a sphere of radius 20) of a "
+                       "3M-Gaussian scene; MLP 8->32->32->1 trained on tile costs of %d other renders" % train_views,
+           "tiles": int(Xt.shape[0]), "train_items": int(X.shape[0]), "train_loss": loss,
+           "collect_s": collect_s, "train_s": train_s,
+           "heldout_mse_log_cost": {"mlp": float(np.mean((pn - ytn) ** 2)), "list_length_fit": float(np.mean((base - ytn) ** 2))}}
+    items = mv.items().cpu().numpy()
+    cyc = dict(zip(items.tolist(), cycles.cpu().numpy().tolist()))
+    workers = 152 * 3
+    times, sim = {}, {}
+    for policy in ("natural", "length", "mlp"):
+        q = mv.queue(policy, model)
+        times[policy] = mv.time_render(q, reps=10, warmup=3)
+        sim[policy] = osc.lpt_makespan([cyc[i] for i in q.cpu().numpy().tolist()], workers)
+    res["batched_render_ms"] = times
+    res["simulated_makespan_cycles"] = sim
+    res["gain_vs_length"] = times["length"] / times["mlp"]
+    res["gain_vs_natural"] = times["natural"] / times["mlp"]
+    return res
+
+
+def bench_large(dev, flush, steps=5, warmup=2):
+    """3840x2160, 6M Gaussians in 256 clusters, SH3: TC forward frame vs FP32 frame, plus backward."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    from paper_2505_24796_gb300 import scenes
+    cam, sc = scenes.large()
+    d = tc.scene_to_device(sc, dev)
+    pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    del pr
+    r = tc.Renderer(cam, len(sc["opacity"]), n + 1024, device=dev, stats=True)
+    r.frame(d, precision="fp32")
+    torch.cuda.synchronize()
+    st = r.stats.to(torch.int64).sum(0).tolist()
+    r.stats = None
+    out = {"workload": "large: 3840x2160, fx=fy=2200, 6M Gaussians (256 clusters, plain distributions), SH3",
+           "splats": n, "alpha_evals": st[0] + st[1]}
+    for prec in ("tc_fp16_split", "fp32"):
+        stg = [_events_ms(lambda: r.project(d), steps, warmup, flush),
+               _events_ms(lambda: r.bin_sort(), steps, warmup, flush),
+               _events_ms(lambda: r.render(d["opacity"], prec), steps, warmup, flush)]
+        out[prec] = {"stages_ms": dict(zip(["project", "bin_sort", "render_fwd"], stg)), "frame_ms": sum(stg),
+                     "frames_per_s": 1000.0 / sum(stg)}
+    out["speedup_render"] = out["fp32"]["stages_ms"]["render_fwd"] / out["tc_fp16_split"]["stages_ms"]["render_fwd"]
+    out["speedup_frame"] = out["fp32"]["frame_ms"] / out["tc_fp16_split"]["frame_ms"]
+    r.render(d["opacity"], "fp32")
+    gimg = torch.ones_like(r.out["img"])
+    P = len(sc["opacity"])
+    grads = dict(dmean2d=torch.zeros(P, 2, device=dev), dconic=torch.zeros(P, 3, device=dev),
+                 dopacity=torch.zeros(P, device=dev), drgb=torch.zeros(P, 3, device=dev))
+    opts = tc.render_opts("fp32")
+    out["render_bwd_ms"] = _events_ms(lambda: tc.tcgs_render_bwd(
+        r.cam, opts, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"], r.proj["conic"], d["opacity"],
+        r.proj["rgb"], r.out["img"], r.out["T_final"], r.out["n_contrib"], gimg, grads=grads), 3, 1, flush)
+    del r
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -355,6 +513,19 @@ def run_tcgs(args):
     rl_proj["frac"] = rl_proj["achieved"] / rl_proj["peak"]
     roof = {"project": rl_proj, "bin_sort": rl_bin, "render_fwd": rl_render}[dominant]
 
+    extras = {}
+    if not args.no_extras:
+        del r
+        torch.cuda.empty_cache()
+        for name, fn in (("differentiation", lambda: bench_differentiation(dev, flush)),
+                         ("scheduler", lambda: bench_scheduler(dev, args.sched_train_views)),
+                         ("large", lambda: bench_large(dev, flush))):
+            try:
+                extras[name] = fn()
+            except Exception as e:   # report, do not hide: the headline line is still printed
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -378,6 +549,7 @@ def run_tcgs(args):
         "gpu_launches": int(launches_per_frame * args.steps), "gpu_launches_per_frame": int(launches_per_frame),
         "gpu_launches_counted_in_capture": int(launches_total),
         "clocks": clocks,
+        "workloads": extras,
     }
     print(json.dumps(line))
     if world > 1:
