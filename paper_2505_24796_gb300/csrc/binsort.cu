@@ -24,8 +24,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 8;                       // keys per thread per tile
-constexpr int kTileItems = kThreads * kItems;   // 2048 keys per tile
+constexpr int kItems = 8;                       // keys per thread per tile (P-sized passes: 2048 per tile)
+constexpr int kItemsSplat = 8;                  // splat passes (16 costs 128 registers and 2 CTAs/SM: slower)
 constexpr int kRadix = 256;
 constexpr int kMaxBlocks = 1024;
 constexpr int kScanBlocks = 1024;
@@ -34,11 +34,12 @@ __device__ __forceinline__ uint32_t load_n(uint32_t n_host, const uint32_t* n_de
     return n_dev ? *n_dev : n_host;
 }
 
+template <int TI>
 __device__ __forceinline__ void block_range(uint32_t n, int G, uint32_t& lo, uint32_t& hi) {
-    uint32_t tiles = (n + kTileItems - 1) / kTileItems;
+    uint32_t tiles = (n + TI - 1) / TI;
     uint32_t per = (tiles + G - 1) / G;
-    uint64_t l = (uint64_t)blockIdx.x * per * kTileItems;
-    uint64_t h = l + (uint64_t)per * kTileItems;
+    uint64_t l = (uint64_t)blockIdx.x * per * TI;
+    uint64_t h = l + (uint64_t)per * TI;
     lo = (uint32_t)(l < n ? l : n);
     hi = (uint32_t)(h < n ? h : n);
 }
@@ -74,6 +75,7 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* warp_sums, T& total) {
 
 // ---------------------------------------------------------------- radix sort passes
 
+template <int KI>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
                                                          const uint32_t* n_dev, int shift, int G,
                                                          uint32_t* __restrict__ hist,
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
     for (int w = 0; w < kWarps; ++w) h[w][t] = 0;
     __syncthreads();
     uint32_t lo, hi;
-    block_range(load_n(n_host, n_dev), G, lo, hi);
+    block_range<kThreads * KI>(load_n(n_host, n_dev), G, lo, hi);
     for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & 0xFFu], 1u);
     __syncthreads();
     uint32_t s = 0;
@@ -118,47 +120,61 @@ __global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ 
     if (d == 0) digit_total_next[t] = 0u;
 }
 
-// Stable scatter of one 8-bit digit.  Per 2048-key tile: warp-level ranks (__match_any_sync), a
-// per-digit prefix over the warps, keys regrouped by digit in shared memory, then written out so
-// that consecutive threads write consecutive addresses of each digit's run (coalesced).
+// Stable scatter of one 8-bit digit.  Per tile of kThreads x KI keys: warp-level ranks
+// (__match_any_sync), a per-digit prefix over the warps, keys and values regrouped by digit in
+// shared memory, then written out so that consecutive threads write consecutive addresses of each
+// digit's run (coalesced).  Keys of the next tile are loaded one tile ahead; values are loaded once
+// the keys are ranked.
+template <int KI>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, uint32_t n_host,
                                                             const uint32_t* n_dev, int shift, int G,
                                                             const uint32_t* __restrict__ offsets) {
+    constexpr int TI = kThreads * KI;
     __shared__ uint32_t wcnt[kWarps][kRadix];
     __shared__ uint32_t boff[kRadix];     // next global position of each digit for this block
     __shared__ uint32_t tstart[kRadix];   // tile-local start of each digit's run
     __shared__ uint32_t ws[kWarps];
-    __shared__ uint32_t sk[kTileItems], sv[kTileItems];
+    __shared__ uint32_t sk[TI], sv[TI];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     uint32_t lo, hi;
-    block_range(load_n(n_host, n_dev), G, lo, hi);
+    block_range<TI>(load_n(n_host, n_dev), G, lo, hi);
     boff[t] = offsets[(size_t)t * G + blockIdx.x];
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (uint32_t tile = lo; tile < hi; tile += kTileItems) {
-        const uint32_t tile_n = hi - tile < (uint32_t)kTileItems ? hi - tile : (uint32_t)kTileItems;
+    uint32_t kn[KI];
+    auto load_keys = [&](uint32_t tile) {
+        const uint32_t base = tile + (uint32_t)warp * (32 * KI);
+#pragma unroll
+        for (int r = 0; r < KI; ++r) {
+            const uint32_t i = base + r * 32 + lane;
+            kn[r] = i < hi ? keys_in[i] : 0u;
+        }
+    };
+    if (lo < hi) load_keys(lo);
+    for (uint32_t tile = lo; tile < hi; tile += TI) {
+        const uint32_t tile_n = hi - tile < (uint32_t)TI ? hi - tile : (uint32_t)TI;
+        const uint32_t base = tile + (uint32_t)warp * (32 * KI);
+        uint32_t k[KI], pos[KI];
+#pragma unroll
+        for (int r = 0; r < KI; ++r) k[r] = kn[r];
+        if (tile + TI < hi) load_keys(tile + TI);
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) wcnt[w][t] = 0;
         __syncthreads();
-        uint32_t k[kItems], v[kItems], rank[kItems], dg[kItems];
-        const uint32_t base = tile + (uint32_t)warp * (32 * kItems);
+        // pos[r] holds (digit << 16) | rank-in-warp, digit 0x100 marking an item past the end
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-            const uint32_t i = base + r * 32 + lane;
-            const bool valid = i < hi;
-            k[r] = valid ? keys_in[i] : 0u;
-            v[r] = valid ? vals_in[i] : 0u;
+        for (int r = 0; r < KI; ++r) {
+            const bool valid = base + r * 32 + lane < hi;
             const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u | lane);
-            dg[r] = d;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             uint32_t before = 0;
             if (valid) before = wcnt[warp][d];
             __syncwarp();
             if (valid && lane == 31 - __clz(peers)) wcnt[warp][d] = before + __popc(peers);
             __syncwarp();
-            rank[r] = before + __popc(peers & lt_mask);
+            pos[r] = ((valid ? d : 0x100u) << 16) | (before + __popc(peers & lt_mask));
         }
         __syncthreads();
         // digit t: exclusive prefix over warps, the tile's count, and the tile-local run start
@@ -173,16 +189,23 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
         tstart[t] = block_exclusive_scan<uint32_t, kThreads>(total, ws, tile_total);
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-            if (dg[r] < 0x100u) {
-                const uint32_t lp = tstart[dg[r]] + wcnt[warp][dg[r]] + rank[r];
+        for (int r = 0; r < KI; ++r) {
+            const uint32_t d = pos[r] >> 16;
+            if (d < 0x100u) {
+                const uint32_t lp = tstart[d] + wcnt[warp][d] + (pos[r] & 0xFFFFu);
                 sk[lp] = k[r];
-                sv[lp] = v[r];
+                pos[r] = lp;
+            } else {
+                pos[r] = 0xFFFFFFFFu;
             }
+        }
+#pragma unroll
+        for (int r = 0; r < KI; ++r) {
+            if (pos[r] != 0xFFFFFFFFu) sv[pos[r]] = vals_in[base + r * 32 + lane];
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kItems; ++q) {
+        for (int q = 0; q < KI; ++q) {
             const uint32_t i = (uint32_t)t + (uint32_t)q * kThreads;
             if (i < tile_n) {
                 const uint32_t key = sk[i];
@@ -335,14 +358,35 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
     }
 }
 
+// Tile ranges from tile-id changes of the sorted keys; each thread checks 4 consecutive keys
+// (one 16-byte load, the two neighbours from the same cache lines).
 __global__ void __launch_bounds__(kThreads) k_ranges(const uint32_t* __restrict__ tile_keys,
                                                      const uint32_t* __restrict__ n_u32,
                                                      uint32_t* __restrict__ ranges) {
-    uint32_t n = *n_u32;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t t = tile_keys[i];
-        if (i == 0 || tile_keys[i - 1] != t) ranges[2 * t] = i;
-        if (i == n - 1 || tile_keys[i + 1] != t) ranges[2 * t + 1] = i + 1;
+    const uint32_t n = *n_u32;
+    const uint32_t quads = (n + 3) / 4;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * q;
+        uint32_t k[4];
+        if (i0 + 3 < n) {
+            const uint4 v = reinterpret_cast<const uint4*>(tile_keys)[q];
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? tile_keys[i0 + j] : 0xFFFFFFFFu;
+        }
+        const uint32_t prev = i0 > 0 ? tile_keys[i0 - 1] : 0xFFFFFFFFu;
+        const uint32_t next = i0 + 4 < n ? tile_keys[i0 + 4] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t i = i0 + j;
+            if (i < n) {
+                const uint32_t before = j == 0 ? prev : k[j - 1];
+                const uint32_t after = j == 3 ? next : k[j + 1];
+                if (i == 0 || before != k[j]) ranges[2 * k[j]] = i;
+                if (i == n - 1 || after != k[j]) ranges[2 * k[j] + 1] = i + 1;
+            }
+        }
     }
 }
 
@@ -377,23 +421,45 @@ inline Workspace layout(char* base, int64_t P, int64_t cap) {
     return w;
 }
 
+// Blocks of the scatter kernel resident at once on the current device (one full wave: each block
+// then walks a contiguous run of tiles, and no second, partly filled wave is left at the end).
+template <int KI>
+inline int resident_sort_blocks() {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 256;
+    if (dev != cached_dev) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter<KI>, kThreads, 0);
+        cached = sms * (per_sm > 0 ? per_sm : 1);
+        if (cached < 1) cached = 256;
+        if (cached > kMaxBlocks) cached = kMaxBlocks;
+        cached_dev = dev;
+    }
+    return cached;
+}
+
+template <int KI>
 inline int sort_blocks(int64_t n) {
-    int64_t tiles = (n + kTileItems - 1) / kTileItems;
+    int64_t tiles = (n + kThreads * KI - 1) / (kThreads * KI);
     if (tiles < 1) tiles = 1;
-    return (int)(tiles < kMaxBlocks ? tiles : kMaxBlocks);
+    const int wave = resident_sort_blocks<KI>();
+    return (int)(tiles < wave ? tiles : wave);
 }
 
 // One LSD pass; digit totals ping-pong between two 256-word buffers (the scan of a pass zeroes
 // the buffer the next pass accumulates into).
+template <int KI>
 inline void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n_host,
                        const uint32_t* n_dev, int shift, int G, const Workspace& w, int pass, cudaStream_t s) {
     uint32_t* tot = w.digit_total + (pass & 1) * kRadix;
     uint32_t* nxt = w.digit_total + ((pass + 1) & 1) * kRadix;
-    k_radix_hist<<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, G, w.hist, tot);
+    k_radix_hist<KI><<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, G, w.hist, tot);
     count_launches(1);
     k_radix_scan<<<kRadix, kThreads, 0, s>>>(w.hist, tot, nxt, G);
     count_launches(1);
-    k_radix_scatter<<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, G, w.hist);
+    k_radix_scatter<KI><<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, G, w.hist);
     count_launches(1);
 }
 
@@ -435,10 +501,10 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     // 1. depth order (4 passes; the result returns to the a-buffers)
     int pass = 0;
     if (P > 0) {
-        int Gp = sort_blocks(P);
+        int Gp = sort_blocks<kItems>(P);
         for (int sh = 0; sh < 32; sh += 8, ++pass) {
             bool even = (pass & 1) == 0;
-            radix_pass(even ? w.dk_a : w.dk_b, even ? w.dv_a : w.dv_b, even ? w.dk_b : w.dk_a,
+            radix_pass<kItems>(even ? w.dk_a : w.dk_b, even ? w.dv_a : w.dv_b, even ? w.dk_b : w.dk_a,
                        even ? w.dv_b : w.dv_a, (uint32_t)P, nullptr, sh, Gp, w, pass, s);
         }
         TCGS_CHECK_LAUNCH();
@@ -469,14 +535,14 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 4. stable sort by tile id
-    int Gs = sort_blocks(splat_capacity);
+    int Gs = sort_blocks<kItemsSplat>(splat_capacity);
     for (int tp = 0; tp < tpasses; ++tp, ++pass) {
-        radix_pass(kbuf[src], vbuf[src], kbuf[src ^ 1], vbuf[src ^ 1], 0u, w.n_u32, 8 * tp, Gs, w, pass, s);
+        radix_pass<kItemsSplat>(kbuf[src], vbuf[src], kbuf[src ^ 1], vbuf[src ^ 1], 0u, w.n_u32, 8 * tp, Gs, w, pass, s);
         src ^= 1;
     }
     TCGS_CHECK_LAUNCH();
     // 5. ranges
-    int Gr = sort_blocks(splat_capacity) * 4;
+    int Gr = sort_blocks<kItemsSplat>(splat_capacity) * 4;
     k_ranges<<<Gr, kThreads, 0, s>>>(kbuf[src], w.n_u32, tile_ranges);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
@@ -539,12 +605,12 @@ extern "C" tcgs_status tcgs_sched_order(const float* cost, const uint32_t* items
     Workspace w = {};
     w.hist = o.hist;
     w.digit_total = o.digit_total;
-    const int G = sort_blocks(n);
+    const int G = sort_blocks<kItems>(n);
     // 0 -> 1 -> 0 -> 1 -> out
-    radix_pass(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 0, G, w, 0, s);
-    radix_pass(o.k1, o.v1, o.k0, o.v0, (uint32_t)n, nullptr, 8, G, w, 1, s);
-    radix_pass(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 16, G, w, 2, s);
-    radix_pass(o.k1, o.v1, o.k0, queue_out, (uint32_t)n, nullptr, 24, G, w, 3, s);
+    radix_pass<kItems>(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 0, G, w, 0, s);
+    radix_pass<kItems>(o.k1, o.v1, o.k0, o.v0, (uint32_t)n, nullptr, 8, G, w, 1, s);
+    radix_pass<kItems>(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 16, G, w, 2, s);
+    radix_pass<kItems>(o.k1, o.v1, o.k0, queue_out, (uint32_t)n, nullptr, 24, G, w, 3, s);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }
