@@ -323,6 +323,49 @@ def bench_large(dev, flush, steps=5, warmup=2):
     return out
 
 
+ABLATION = [
+    # (label, precision, early_cull, tile_cull): Table 4 (EarlyCull x Frag2Mat with G2L) ...
+    ("fp32", "fp32", False, True),
+    ("fp32+earlycull", "fp32", True, True),
+    ("frag2mat_g2l_fp16", "tc_fp16", False, False),
+    ("frag2mat_g2l_fp16+earlycull", "tc_fp16", True, False),
+    ("frag2mat_g2l_fp16+earlycull+block_marks", "tc_fp16", True, True),
+    # ... Table 5 (Frag2Mat without G2L) and the other encodings of this renderer
+    ("frag2mat_global_fp16", "tc_fp16_global", True, False),
+    ("frag2mat_global_tf32", "tc_tf32_global", True, False),
+    ("frag2mat_g2l_tf32", "tc_tf32", True, True),
+    ("frag2mat_g2l_fp8_split", "tc_fp8", True, True),
+    ("frag2mat_g2l_fp16_split", "tc_fp16_split", True, True),
+]
+
+
+def bench_ablation(r, dsc, flush, img32, oracle_img=None, mask=None, reps=10, warmup=3):
+    """Render-stage time and accuracy of each configuration of ABLATION on one frame's bins."""
+    import torch
+    out = {}
+    ref32 = img32.cpu().numpy().astype(np.float64)
+    for label, prec, ec, tcull in ABLATION:
+        fn = lambda: r.render(dsc["opacity"], prec, early_cull=ec, tile_cull=tcull)
+        ms = _events_ms(fn, reps, warmup, flush)
+        fn()
+        torch.cuda.synchronize()
+        im = r.out["img"].cpu().numpy().astype(np.float64)
+        row = {"precision": prec, "early_cull": ec, "block_marks": tcull and not prec.endswith("_global"),
+               "render_ms": ms, "finite": bool(np.isfinite(im).all())}
+        mse = float(np.mean((im - ref32) ** 2))
+        row["psnr_vs_fp32_db"] = 10 * math.log10(1 / mse) if mse > 0 else None
+        if oracle_img is not None:
+            d = (im - oracle_img)[:, mask]
+            mse = float(np.mean(d ** 2))
+            row["psnr_vs_oracle_db"] = 10 * math.log10(1 / mse) if mse > 0 else None
+            row["within_2e-3_vs_oracle"] = float((np.abs(d).max(axis=0) <= 2e-3).mean())
+        out[label] = row
+    base = out["fp32"]["render_ms"]
+    for row in out.values():
+        row["speedup_vs_fp32"] = base / row["render_ms"]
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_tcgs(args):
@@ -461,6 +504,7 @@ def run_tcgs(args):
         return
 
     # --- accuracy of this frame: TC vs FP32 on the GPU, and vs the FP64 oracle on the sampled tiles
+    oimg, mask = None, None
     img_tc_np = img_tc.cpu().numpy().astype(np.float64)
     img32_np = img_fp32.cpu().numpy().astype(np.float64)
     mse_tc_fp32 = float(np.mean((img_tc_np - img32_np) ** 2))
@@ -485,6 +529,9 @@ def run_tcgs(args):
             acc[f"within_2e-3_{name}"] = float((np.abs(d).max(axis=0) <= 2e-3).mean())
             acc[f"max_abs_{name}"] = float(np.abs(d).max())
         acc["oracle_pixels_compared"] = int(mask.sum())
+    ablation = None
+    if not args.no_extras:
+        ablation = bench_ablation(r, dsc, flush, img_fp32, oimg, mask)
 
     # --- roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -550,6 +597,7 @@ def run_tcgs(args):
         "gpu_launches_counted_in_capture": int(launches_total),
         "clocks": clocks,
         "workloads": extras,
+        "ablation": ablation,
     }
     print(json.dumps(line))
     if world > 1:

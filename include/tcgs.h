@@ -60,7 +60,15 @@ typedef enum {
     TCGS_TC_FP16 = 1,       /* Frag2Mat + G2L on tensor cores, FP16 inputs, FP32 accumulate, with
                                the paper's K = 8 padding (v0 / 3 in three slots, Sec. 5.1) */
     TCGS_TC_FP16_SPLIT = 2, /* as TC_FP16 but v = v_hi + v_lo in FP16 over K = 16 (u duplicated) */
-    TCGS_TC_FP8 = 3         /* trial: U and V in FP8 e4m3, FP32 accumulate (accuracy reported only) */
+    TCGS_TC_FP8 = 3,        /* trial: Frag2Mat + G2L on FP8 e4m3 inputs (K = 32 per MMA): u = u_hi + u_lo
+                               exactly, v = v_hi + v_lo + v_lo2, power-of-two column scales; FP32
+                               accumulate (accuracy reported; not a faster path) */
+    TCGS_TC_TF32 = 4,       /* Frag2Mat + G2L on TF32 inputs (K = 8 per MMA), FP32 accumulate */
+    TCGS_TC_FP16_GLOBAL = 5,/* ablation of Table 5: Frag2Mat WITHOUT G2L, u and v in global pixel
+                               coordinates, FP16 inputs in the TC_FP16 layout (overflows to inf past
+                               256 px; non-finite exponents are culled).  Every list entry is walked
+                               (tile_cull ignored).  tcgs_render_fwd and tcgs_frag2mat_beta only */
+    TCGS_TC_TF32_GLOBAL = 6 /* ablation of Table 5: as TC_FP16_GLOBAL with TF32 inputs */
 } tcgs_precision;
 
 /* Pinhole camera.  mean2d = (fx X / Z + cx, fy Y / Z + cy) for camera-space (X, Y, Z). */
@@ -77,7 +85,10 @@ typedef struct {
 typedef struct {
     int32_t precision;       /* tcgs_precision */
     float alpha_max;         /* alpha clamp (0.99 as in the official 3DGS renderer; 1 = Algorithm 1 literally) */
-    int32_t early_cull;      /* FP32 path only: test beta < -ln 255 before exp (Sec. 4.1); TC paths always do */
+    int32_t early_cull;      /* 1 = EarlyCull (Sec. 4.1): cull on beta < -ln 255, tested before the exponential;
+                                0 = cull on alpha < 1/255 after it (Eq. 5, the 3DGS baseline).  On the TC paths
+                                the walk is branch-free and evaluates ex2 for every walked fragment either way:
+                                the option changes the test, not the work */
     int32_t tile_cull;       /* TC paths: 1 = skip, per 8x4 pixel block, list entries whose Gaussian cannot
                                 reach alpha >= 1/255 at any pixel of the block (exact minimum of the conic
                                 form over the block; the image is unchanged); 0 = walk every entry */
@@ -219,7 +230,7 @@ typedef struct {
  * counter and renders that tile exactly as tcgs_render_fwd does (same per-tile body, so every image
  * is identical to a per-view launch whatever the queue order).  An item is (view << 16) | tile.
  * The order of `queue` decides the schedule only: a longest-predicted-first order shortens the
- * makespan when tile costs are uneven.  TC precisions only (FP16 or FP16_SPLIT).
+ * makespan when tile costs are uneven.  TC precisions with G2L only (not the *_GLOBAL ablations).
  * In:  n_views in [1, TCGS_MAX_VIEWS] views (host array of tcgs_view), opacity [P] shared by all
  *      views, bg3 host float[3], queue: device [n_items] uint32.
  * work_counter: device uint32, scratch (reset by the call on `stream`).
@@ -296,12 +307,13 @@ TCGS_API tcgs_status tcgs_render_bwd(const tcgs_camera* cam /* host */, const tc
                             float* dopacity, float* drgb, tcgs_stream stream);
 
 /*
- * Frag2Mat exponents as the tensor cores compute them (Eq. 18, G2L frame of Sec. 4.3), for
- * inspection against the error bound of Appendix A.  For each of n_tiles tiles (device
+ * Frag2Mat exponents as the tensor cores compute them (Eq. 18; in the G2L frame of Sec. 4.3, or
+ * in global pixel coordinates for the *_GLOBAL ablations), for inspection against the error bound
+ * of Appendix A.  For each of n_tiles tiles (device
  * tiles[n_tiles] int32) and each of the first min(max_n, n(T)) list entries, writes
  * beta_hat in natural-log units to beta_out [n_tiles, 256, max_n] (pixel-major within the tile,
  * row-major pixels; entries past the list end are set to -INFINITY).
- * precision: TCGS_TC_FP16 or TCGS_TC_FP16_SPLIT (or TCGS_TC_FP8).
+ * precision: any TC precision (TC_FP16, TC_FP16_SPLIT, TC_FP8, TC_TF32, TC_FP16_GLOBAL, TC_TF32_GLOBAL).
  */
 TCGS_API tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam /* host */, int32_t precision, const uint32_t* tile_ranges,
                                const uint32_t* ids_sorted, const float* mean2d, const float* conic,

@@ -1,5 +1,7 @@
 """Frag2Mat and G2L in FP64 (Sec. 4.2 and 4.3) plus the tensor-core error
-bound of Appendix A (Proposition "dot product").
+bound of Appendix A (Proposition "dot product"), and the input roundings of the
+tensor-core encodings it is checked against (FP16, TF32, FP8 e4m3), with the
+error bound of the FP8 split encoding derived from them.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
@@ -17,6 +19,9 @@ import numpy as np
 EPS_H = 2.0 ** -10      # Table "floating points": FP16 / TF32 machine epsilon (9.77e-4)
 EPS_F = 2.0 ** -23      # FP32 machine epsilon (1.19e-7)
 TILE = 16
+# FP8 encoding: column i of u is scaled by 2^-a_i and of v by 2^a_i before the split
+FP8_COLUMN_EXP = (0, 2, 2, 6, 6, 6)
+E4M3_MAX = 448.0
 
 
 def tile_centre(tx: int, ty: int):
@@ -79,3 +84,62 @@ def paper_bound(absum) -> np.ndarray:
 
 def round_f16(a) -> np.ndarray:
     return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+
+
+def global_products(tx: int, ty: int, mean2d, conic, opacity, half: int | None = None):
+    """U, V in global pixel coordinates for the pixels of tile (tx, ty) (Frag2Mat without G2L, the
+    ablation of Table 5), exact beta = U V^T and sum |u_i v_i|."""
+    c = tile_centre(tx, ty)
+    dx, dy = tile_pixels_local(half)
+    U = pixel_vectors(dx + c[0], dy + c[1])
+    V = gaussian_vectors(mean2d, conic, opacity)
+    return U, V, U @ V.T, np.abs(U) @ np.abs(V).T
+
+
+def round_tf32(a) -> np.ndarray:
+    """Round to TF32 (1 + 10 fraction bits, FP32 exponent range), to nearest with ties away from
+    zero."""
+    a = np.asarray(a, np.float64)
+    m, e = np.frexp(a)                      # a = m 2^e, 0.5 <= |m| < 1
+    q = np.sign(m) * np.floor(np.abs(m) * 2.0 ** 11 + 0.5)
+    return np.ldexp(q / 2.0 ** 11, e)
+
+
+def round_e4m3(a) -> np.ndarray:
+    """Round to the FP8 e4m3 format (4 exponent bits, bias 7, 3 fraction bits; largest finite value
+    448, smallest subnormal 2^-9), to nearest even, saturating at +-448."""
+    a = np.asarray(a, np.float64)
+    x = np.abs(a)
+    e = np.maximum(np.floor(np.log2(np.maximum(x, 2.0 ** -9))), -6.0)   # subnormals share 2^-6's spacing
+    q = 2.0 ** (e - 3)
+    return np.sign(a) * np.minimum(np.round(x / q) * q, E4M3_MAX)
+
+
+def fp8_split(U, V):
+    """The FP8 split encoding: column-scaled u' = u 2^-a = u_hi + u_lo and v' = v 2^a ~ v_hi + v_lo +
+    v_lo2, each part an e4m3 number; returns the exponent that the five groups of products
+    u_hi (v_hi + v_lo + v_lo2) + u_lo (v_hi + v_lo) evaluate to, in FP64."""
+    s = 2.0 ** -np.asarray(FP8_COLUMN_EXP, np.float64)
+    u = np.asarray(U, np.float64) * s
+    v = np.asarray(V, np.float64) / s
+    uh = round_e4m3(u); ul = round_e4m3(u - uh)
+    vh = round_e4m3(v); r1 = v - vh
+    vl = round_e4m3(r1); vl2 = round_e4m3(r1 - vl)
+    return uh @ (vh + vl + vl2).T + ul @ (vh + vl).T
+
+
+def fp8_split_bound(U, V, log2_scale: bool = False) -> np.ndarray:
+    """|beta_hat - beta| of the FP8 split encoding, before accumulation rounding, when u' splits
+    exactly and |v'| <= 448.  Each e4m3 rounding errs by at most max(2^-4 |x|, 2^-10), so the v
+    residuals after one and after three parts obey |r2| <= max(2^-8 |v'|, 2^-10) and
+    |r3| <= max(2^-12 |v'|, 2^-10); the products evaluate u' v' - u_hi r3 - u_lo r2 with
+    |u_hi| <= (1 + 2^-4) |u'| and |u_lo| <= 2^-4 |u'|.  The 2^-10 floor applies to v in the units
+    the kernel encodes (log2 units): with log2_scale = False, V is in natural-log units and the
+    floor is converted."""
+    s = 2.0 ** -np.asarray(FP8_COLUMN_EXP, np.float64)
+    aU, aV = np.abs(np.asarray(U, np.float64)), np.abs(np.asarray(V, np.float64))
+    rel = ((1 + 2.0 ** -4) * 2.0 ** -12 + 2.0 ** -4 * 2.0 ** -8) * (aU @ aV.T)
+    floor = (1 + 2.0 ** -4 + 2.0 ** -4) * 2.0 ** -10 * (aU @ s)
+    if not log2_scale:
+        floor = floor * np.log(2.0)
+    return rel + floor[:, None]

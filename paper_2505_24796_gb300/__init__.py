@@ -18,7 +18,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS_TC_FP8, TcgsError, check,
+from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_GLOBAL, TCGS_TC_FP16_SPLIT, TCGS_TC_FP8,
+                   TCGS_TC_TF32, TCGS_TC_TF32_GLOBAL, TcgsError, check,
                    tcgs_camera, tcgs_render_opts)
 
 TILE = 16
@@ -26,7 +27,8 @@ TILE = 16
 __all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
            "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "TcgsError", "PRECISIONS",
-           "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8"]
+           "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
+           "TCGS_TC_TF32_GLOBAL"]
 
 
 def _L():
@@ -73,12 +75,14 @@ def _cam(cam) -> tcgs_camera:
     return cam if isinstance(cam, tcgs_camera) else make_camera(cam)
 
 
-def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=False, tile_stats=None,
+def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=None, tile_stats=None,
                 device_status=None, tile_cull=True) -> tcgs_render_opts:
+    """early_cull None: the path's default (off on the FP32 path, the 3DGS baseline; on for the
+    tensor-core paths, as the paper's renderer)."""
     o = tcgs_render_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.alpha_max = float(alpha_max)
-    o.early_cull = int(bool(early_cull))
+    o.early_cull = int(o.precision != TCGS_FP32) if early_cull is None else int(bool(early_cull))
     o.tile_cull = int(bool(tile_cull))
     o.tile_stats = _ptr(tile_stats, torch.int32, "tile_stats") if tile_stats is not None else None
     o.device_status = _ptr(device_status, torch.int32, "device_status") if device_status is not None else None
@@ -341,7 +345,7 @@ class Renderer:
         return tcgs_bin_sort(self.cam, self.proj["mean2d"], self.proj["radius"], self.proj["depth"], self.capacity,
                              workspace=self.ws, out=self.bins, stream=stream)
 
-    def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=False, bg=(0, 0, 0),
+    def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=None, bg=(0, 0, 0),
                stream=None, tile_cull=True):
         opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status, tile_cull)
         return tcgs_render_fwd(self.cam, opts, self.bins["tile_ranges"], self.bins["ids_sorted"],

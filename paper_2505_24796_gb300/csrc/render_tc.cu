@@ -18,10 +18,17 @@
 //     transpose, no cross-lane scan);
 //   - EarlyCull compares log2(alpha) with -log2(255) before ex2; survivors are blended in FP32,
 //     branch-free (selects), so a warp never diverges inside the walk.
-// Two precisions share the kernel:
-//   TC_FP16        the paper's K = 8 layout (v0 / 3 in three slots, u's 1 in three slots),
-//   TC_FP16_SPLIT  v = v_hi + v_lo (both FP16) with u duplicated: 12 of the 16 K slots,
-//                  same single MMA, about 22-bit accuracy of v.
+// Every precision uses 32-byte operand rows (one MMA of K = 32 bytes per half tile):
+//   TC_FP16        kind::f16, the paper's K = 8 layout (v0 / 3 in three slots, u's 1 in three slots),
+//   TC_FP16_SPLIT  kind::f16, v = v_hi + v_lo (both FP16) with u duplicated: 12 of the 16 K slots,
+//                  same single MMA, about 22-bit accuracy of v,
+//   TC_TF32        kind::tf32, K = 8: u and v rounded to TF32 (round to nearest, ties away),
+//   TC_FP8         kind::f8f6f4, K = 32, e4m3: u = u_hi + u_lo (exact) and v = v_hi + v_lo + v_lo2,
+//                  with power-of-two column scales that keep every part inside the e4m3 range;
+//                  five groups of six products, u_hi (v_hi + v_lo + v_lo2) + u_lo (v_hi + v_lo),
+//   TC_FP16_GLOBAL / TC_TF32_GLOBAL  the ablation of Table 5: Frag2Mat without G2L, u and v in
+//                  global pixel coordinates (FP16 overflows past 256 px, as the paper observes);
+//                  these walk every list entry of the tile (no FP32 reach test, no block marks).
 // The block marks only skip list entries that Algorithm 1 would cull at every pixel of the block
 // (the minimum over the block's pixel-centre rectangle bounds every pixel), so the image is that of
 // Algorithm 1; with tile_cull = 0 every entry is walked.
@@ -29,6 +36,8 @@
 // releases its TMEM; an MMA issued for a batch that is not walked is waited for before release.
 // Two accumulator buffers let the MMAs of batch k+1 run while batch k is walked; only thread 0 polls
 // the mbarrier, the others wait in a hardware barrier.
+#include <cuda_fp8.h>
+
 #include <cstring>
 
 #include "common.cuh"
@@ -71,9 +80,16 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = F16 (0), both K-major,
-// N >> 3 at [17,23), M >> 4 at [24,29).
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptors: D = F32 (bit 4), A and B types at [7,10) and [10,13), both K-major,
+// N >> 3 at [17,23), M >> 4 at [24,29).  kind::f16 with F16 = 0; kind::tf32 with TF32 = 2;
+// kind::f8f6f4 with E4M3 = 0.
+constexpr uint32_t kIdescShape = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kIdescF16 = kIdescShape;
+constexpr uint32_t kIdescTf32 = kIdescShape | (2u << 7) | (2u << 10);
+constexpr uint32_t kIdescE4m3 = kIdescShape;
+
+// Operand encodings of a 32-byte K row (see the file comment).
+enum : int { kEncF16Split = 0, kEncF16Pad = 1, kEncTf32 = 2, kEncFp8 = 3 };
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
@@ -121,6 +137,82 @@ __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
     return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
+__device__ __forceinline__ uint32_t tf32_bits(float x) {   // round to TF32 (10 fraction bits)
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t e4m3_bits(float x) {   // round to nearest e4m3, saturating at +-448
+    return (uint32_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+
+__device__ __forceinline__ float e4m3_value(uint32_t b) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3)));
+}
+
+// FP8 column scales 2^-a_i of u (and 2^a_i of v), a = {0, 2, 2, 6, 6, 6}: the scaled tile-local
+// u parts stay exact e4m3 numbers (at least 2^-8) and the scaled v of any Gaussian that can reach
+// the tile stays below 448 (|v0| <= 371, |v1|, |v2| <= 60, |v3|, |v5| <= 2.4, |v4| <= 4.8 in log2
+// units, from the reach test and lambda_max(Q) <= 1 / 0.3).
+__device__ __forceinline__ float fp8_uscale(int i) { return i == 0 ? 1.f : (i < 3 ? 0.25f : 0.015625f); }
+
+// One 32-byte K row of U (kV = false, c = u) or V (kV = true, c = v) in encoding `enc`, as eight
+// 32-bit words in K order.
+template <bool kV>
+__device__ __forceinline__ void encode_row(int enc, const float c[6], uint32_t w[8]) {
+    if (enc == kEncTf32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = tf32_bits(c[k]);
+        w[6] = w[7] = 0u;
+    } else if (enc == kEncFp8) {
+        uint32_t b[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) b[k] = 0u;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float sc = kV ? 1.f / fp8_uscale(k) : fp8_uscale(k);
+            const float x = c[k] * sc;
+            const uint32_t hi = e4m3_bits(x);
+            const float r1 = x - e4m3_value(hi);
+            const uint32_t lo = e4m3_bits(r1);
+            if (kV) {   // [v_hi | v_lo | v_lo2 | v_hi | v_lo]
+                const uint32_t lo2 = e4m3_bits(r1 - e4m3_value(lo));
+                b[k] = hi; b[6 + k] = lo; b[12 + k] = lo2; b[18 + k] = hi; b[24 + k] = lo;
+            } else {    // [u_hi | u_hi | u_hi | u_lo | u_lo]
+                b[k] = hi; b[6 + k] = hi; b[12 + k] = hi; b[18 + k] = lo; b[24 + k] = lo;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = b[4 * q] | (b[4 * q + 1] << 8) | (b[4 * q + 2] << 16) | (b[4 * q + 3] << 24);
+    } else {
+        __half h[16];
+        const __half zero = __float2half_rn(0.f);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) h[k] = zero;
+        if (enc == kEncF16Split) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const __half hi = __float2half_rn(c[k]);
+                h[k] = hi;
+                h[6 + k] = kV ? __float2half_rn(c[k] - __half2float(hi)) : hi;
+            }
+        } else {   // paper padding: [v0/3 x 3, v1..v5] and [1 x 3, u1..u5]
+            const __half c0 = __float2half_rn(kV ? c[0] * (1.f / 3.f) : c[0]);
+            h[0] = h[1] = h[2] = c0;
+#pragma unroll
+            for (int k = 1; k < 6; ++k) h[2 + k] = __float2half_rn(c[k]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = pack2(h[2 * q], h[2 * q + 1]);
+    }
+}
+
+__device__ __forceinline__ void store_row(uint8_t* base, int row, const uint32_t w[8]) {
+    *reinterpret_cast<uint4*>(base + canon_off(row, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(base + canon_off(row, 1)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // Per-view inputs and outputs (the batched renderer walks (view, tile) items of up to
 // TCGS_MAX_VIEWS views; the single-view call uses entry 0).
 struct ViewData {
@@ -141,8 +233,10 @@ struct TcParams {
     const float* opacity;
     float bg[3];
     float alpha_max;
-    int split;
+    int enc;                    // operand encoding (kEnc*)
+    int global;                 // 1: Frag2Mat in global pixel coordinates (ablation, no G2L)
     int tile_cull;
+    int early_cull;             // selects the kernel instance (kEarly)
     int32_t* status;
     int n_views;
     const uint32_t* queue;      // queue mode: items (view << 16 | tile) in the order to render
@@ -201,7 +295,9 @@ __device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float 
     return best;
 }
 
-template <bool kInspect, bool kStats, bool kQueue>
+// kEarly: EarlyCull form of the cull test; kSplit: the default encoding (TC_FP16_SPLIT with G2L)
+// fixed at compile time, otherwise the encoding and frame come from p.
+template <bool kInspect, bool kStats, bool kQueue, bool kEarly, bool kSplit>
 __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar[2];
@@ -222,6 +318,8 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
     const float by0 = 4.f * by - 7.5f, by1 = by0 + 3.f;
     uint8_t* sA = smem + kSmemA;
     const uint32_t mbar0 = smem_u32(&s_mbar[0]);
+    const int enc = kSplit ? (int)kEncF16Split : p.enc;
+    const bool global = kSplit ? false : p.global != 0;
 
     if (producer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -234,25 +332,20 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
             s_timeout = 0;
         }
     } else {
-        // U row t = this thread's pixel, tile-local (G2L: dp = p - p(T)); the same for every tile
-        const float dx = (float)lx + 0.5f - kTile / 2, dy = (float)ly + 0.5f - kTile / 2;
-        __half u[16];
-        const __half one = __float2half_rn(1.f), zero = __float2half_rn(0.f);
-        const __half hx = __float2half_rn(dx), hy = __float2half_rn(dy);
-        const __half hxx = __float2half_rn(dx * dx), hxy = __float2half_rn(dx * dy), hyy = __float2half_rn(dy * dy);
-        if (p.split) {
-            u[0] = one; u[1] = hx; u[2] = hy; u[3] = hxx; u[4] = hxy; u[5] = hyy;
-            u[6] = one; u[7] = hx; u[8] = hy; u[9] = hxx; u[10] = hxy; u[11] = hyy;
-            u[12] = zero; u[13] = zero; u[14] = zero; u[15] = zero;
-        } else {
-            u[0] = one; u[1] = one; u[2] = one; u[3] = hx; u[4] = hy; u[5] = hxx; u[6] = hxy; u[7] = hyy;
-#pragma unroll
-            for (int k = 8; k < 16; ++k) u[k] = zero;
+        // U row t = this thread's pixel, tile-local (G2L: dp = p - p(T)); the same for every tile.
+        // Without G2L (one tile per CTA) it is the global pixel centre of the CTA's tile.
+        float dx = (float)lx + 0.5f - kTile / 2, dy = (float)ly + 0.5f - kTile / 2;
+        if (global && !kQueue) {
+            int tile0 = kInspect ? p.dbg_tiles[blockIdx.x] : (int)blockIdx.x;
+            const int ntiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
+            tile0 = tile0 < 0 || tile0 >= ntiles ? 0 : tile0;   // an invalid tile is reported below
+            dx += (float)((tile0 % p.v[0].cam.grid_w) * kTile + kTile / 2);
+            dy += (float)((tile0 / p.v[0].cam.grid_w) * kTile + kTile / 2);
         }
-        uint4 c0 = make_uint4(pack2(u[0], u[1]), pack2(u[2], u[3]), pack2(u[4], u[5]), pack2(u[6], u[7]));
-        uint4 c1 = make_uint4(pack2(u[8], u[9]), pack2(u[10], u[11]), pack2(u[12], u[13]), pack2(u[14], u[15]));
-        *reinterpret_cast<uint4*>(sA + canon_off(t, 0)) = c0;
-        *reinterpret_cast<uint4*>(sA + canon_off(t, 1)) = c1;
+        const float u[6] = {1.f, dx, dy, dx * dx, dx * dy, dy * dy};
+        uint32_t w[8];
+        encode_row<false>(enc, u, w);
+        store_row(sA, t, w);
     }
     fence_async_smem();
     tc_fence_before();
@@ -311,7 +404,19 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
             float4* sP = reinterpret_cast<float4*>(smem + kSmemP + buf * kPBytes);
             float v[6] = {kCulledV, 0.f, 0.f, 0.f, 0.f, 0.f};
             float mx = 0.f, my = 0.f, lim = -1.f, ia = 0.f, ic = 0.f;
-            if (d.valid) {
+            if (d.valid && global) {
+                // ablation without G2L: Eq. 12 in global coordinates for every listed Gaussian
+                mx = d.mx; my = d.my;
+                const float lno = __logf(d.o);
+                const float qx = d.s11 * mx + d.s12 * my, qy = d.s12 * mx + d.s22 * my;
+                v[0] = (lno - 0.5f * (mx * qx + my * qy)) * kLog2e;
+                v[1] = qx * kLog2e;
+                v[2] = qy * kLog2e;
+                v[3] = -0.5f * d.s11 * kLog2e;
+                v[4] = -d.s12 * kLog2e;
+                v[5] = -0.5f * d.s22 * kLog2e;
+                lim = 3.0e38f;
+            } else if (d.valid) {
                 mx = d.mx - cx; my = d.my - cy;   // G2L mean
                 const float lno = __logf(d.o);
                 // alpha >= 1/255 somewhere needs q <= 2 (ln o + ln 255); relative and absolute
@@ -345,30 +450,13 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
             sP[3 * lane] = make_float4(mx, my, d.s11, d.s12);
             sP[3 * lane + 1] = make_float4(d.s22, lim, ia, ic);
             sP[3 * lane + 2] = make_float4(d.r, d.g, d.b, 0.f);
-            uint8_t* sB = smem + kSmemB + buf * kVBytes;
-            __half h[16];
+            if (!global) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
-            if (p.split) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const __half hi = __float2half_rn(v[k]);
-                    h[k] = hi;
-                    h[6 + k] = __float2half_rn(v[k] - __half2float(hi));
-                }
-                h[12] = h[13] = h[14] = h[15] = __float2half_rn(0.f);
-            } else {
-                const __half third = __float2half_rn(v[0] * (1.f / 3.f));
-                h[0] = h[1] = h[2] = third;
-#pragma unroll
-                for (int k = 1; k < 6; ++k) h[2 + k] = __float2half_rn(v[k]);
-#pragma unroll
-                for (int k = 8; k < 16; ++k) h[k] = __float2half_rn(0.f);
+                for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
             }
-            uint4 c0 = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-            uint4 c1 = make_uint4(pack2(h[8], h[9]), pack2(h[10], h[11]), pack2(h[12], h[13]), pack2(h[14], h[15]));
-            *reinterpret_cast<uint4*>(sB + canon_off(lane, 0)) = c0;
-            *reinterpret_cast<uint4*>(sB + canon_off(lane, 1)) = c1;
+            uint32_t w[8];
+            encode_row<true>(enc, v, w);
+            store_row(smem + kSmemB + buf * kVBytes, lane, w);
             fence_async_smem();
         };
         // Consumer warps: which slots of buffer `buf` can reach alpha >= 1/255 somewhere in this
@@ -388,12 +476,25 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint64_t descA = make_desc(smem_u32(sA + h * 4096));
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                        tmem + (uint32_t)(tb * 2 * kN + h * kN)),
-                    "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
-                    : "memory");
+                const uint32_t dt = tmem + (uint32_t)(tb * 2 * kN + h * kN);
+                if (enc == kEncTf32)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                        "l"(descA), "l"(descB), "r"(kIdescTf32), "r"(0u)
+                        : "memory");
+                else if (enc == kEncFp8)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                        "l"(descA), "l"(descB), "r"(kIdescE4m3), "r"(0u)
+                        : "memory");
+                else
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                        "l"(descA), "l"(descB), "r"(kIdescF16), "r"(0u)
+                        : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              mbar0 + 8u * (uint32_t)tb)
@@ -483,8 +584,11 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
                     m &= m - 1;
                     const float b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
                     tmem_wait_ld();
-                    const bool pass = b2 >= thr;                       // EarlyCull, log2 units
-                    const float a = fminf(p.alpha_max, ex2_approx(b2));
+                    const float e = ex2_approx(b2);
+                    // EarlyCull compares log2(alpha) with -log2(255); without it alpha itself is
+                    // compared with 1/255 (thr is infinite once the pixel has terminated)
+                    const bool pass = kEarly ? b2 >= thr : (e >= kCullAlpha && thr < kInf);
+                    const float a = fminf(p.alpha_max, e);
                     const float Tn = fmaf(-a, T, T);
                     const bool term = pass && (Tn < kTmin);           // Algorithm 1: terminate, unblended
                     const bool blend = pass && !term;
@@ -587,20 +691,35 @@ bool device_is_sm103() {
     return g_device_ok;
 }
 
-bool g_attr_set[2][2][2] = {};
+bool g_attr_set[2][2][2][2][2] = {};
 
-template <bool kInspect, bool kStats, bool kQueue>
-tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
-    if (!g_attr_set[kInspect][kStats][kQueue]) {
-        if (cudaFuncSetAttribute(k_render_tc<kInspect, kStats, kQueue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemDyn) != cudaSuccess)
+template <bool kInspect, bool kStats, bool kQueue, bool kEarly, bool kSplit>
+tcgs_status launch_tc_t(const TcParams& p, int blocks, cudaStream_t s) {
+    auto kern = k_render_tc<kInspect, kStats, kQueue, kEarly, kSplit>;
+    if (!g_attr_set[kInspect][kStats][kQueue][kEarly][kSplit]) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
             return TCGS_ERR_CUDA;
-        g_attr_set[kInspect][kStats][kQueue] = true;
+        g_attr_set[kInspect][kStats][kQueue][kEarly][kSplit] = true;
     }
-    k_render_tc<kInspect, kStats, kQueue><<<blocks, kTcThreads, kSmemDyn, s>>>(p);
+    kern<<<blocks, kTcThreads, kSmemDyn, s>>>(p);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
+}
+
+// The cull test and the operand encoding sit in the per-fragment and per-batch paths, so the
+// default configuration (EarlyCull, split encoding, G2L) is an instance of its own; the other
+// encodings and the alpha-form cull test share generic instances.
+template <bool kInspect, bool kStats, bool kQueue>
+tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
+    if constexpr (kInspect) {
+        return launch_tc_t<kInspect, kStats, kQueue, true, false>(p, blocks, s);
+    } else {
+        const bool split = p.enc == kEncF16Split && !p.global;
+        if (!p.early_cull) return launch_tc_t<kInspect, kStats, kQueue, false, false>(p, blocks, s);
+        if (split) return launch_tc_t<kInspect, kStats, kQueue, true, true>(p, blocks, s);
+        return launch_tc_t<kInspect, kStats, kQueue, true, false>(p, blocks, s);
+    }
 }
 
 ViewData make_view(const tcgs_camera* cam, const uint32_t* tile_ranges, const uint32_t* ids, const float* mean2d,
@@ -613,13 +732,30 @@ ViewData make_view(const tcgs_camera* cam, const uint32_t* tile_ranges, const ui
     return v;
 }
 
+bool is_tc_precision(int precision) {
+    return precision == TCGS_TC_FP16 || precision == TCGS_TC_FP16_SPLIT || precision == TCGS_TC_FP8 ||
+           precision == TCGS_TC_TF32 || precision == TCGS_TC_FP16_GLOBAL || precision == TCGS_TC_TF32_GLOBAL;
+}
+
+bool is_global_precision(int precision) {
+    return precision == TCGS_TC_FP16_GLOBAL || precision == TCGS_TC_TF32_GLOBAL;
+}
+
 TcParams base_params(int precision, const float* opacity) {
     TcParams p;
     memset(&p, 0, sizeof(p));
     p.opacity = opacity;
-    p.split = precision == TCGS_TC_FP16_SPLIT;
+    switch (precision) {
+        case TCGS_TC_FP16_SPLIT: p.enc = kEncF16Split; break;
+        case TCGS_TC_TF32:
+        case TCGS_TC_TF32_GLOBAL: p.enc = kEncTf32; break;
+        case TCGS_TC_FP8: p.enc = kEncFp8; break;
+        default: p.enc = kEncF16Pad; break;   // TC_FP16, TC_FP16_GLOBAL
+    }
+    p.global = is_global_precision(precision) ? 1 : 0;
     p.alpha_max = 0.99f;
     p.tile_cull = 1;
+    p.early_cull = 1;
     return p;
 }
 
@@ -636,7 +772,8 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
     for (int i = 0; i < 3; ++i) p.bg[i] = bg3 ? bg3[i] : 0.f;
     p.alpha_max = opts->alpha_max;
     p.status = opts->device_status;
-    p.tile_cull = opts->tile_cull;
+    p.tile_cull = p.global ? 0 : opts->tile_cull;   // the ablation walks every entry
+    p.early_cull = opts->early_cull;
     const int tiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
     return opts->tile_stats ? launch_tc<false, true, false>(p, tiles, s) : launch_tc<false, false, false>(p, tiles, s);
 }
@@ -667,6 +804,10 @@ extern "C" tcgs_status tcgs_render_fwd(const tcgs_camera* cam, const tcgs_render
                                       T_final, n_contrib, s);
         case TCGS_TC_FP16:
         case TCGS_TC_FP16_SPLIT:
+        case TCGS_TC_FP8:
+        case TCGS_TC_TF32:
+        case TCGS_TC_FP16_GLOBAL:
+        case TCGS_TC_TF32_GLOBAL:
             return launch_render_tc(cam, opts, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, bg3, img,
                                     T_final, n_contrib, s);
         default:
@@ -682,7 +823,7 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     if (n_views < 1 || n_views > TCGS_MAX_VIEWS || !views || !opts || !opacity || n_items < 0 ||
         (n_items > 0 && (!queue || !work_counter)))
         return TCGS_ERR_INVALID;
-    if (opts->precision != TCGS_TC_FP16 && opts->precision != TCGS_TC_FP16_SPLIT) return TCGS_ERR_INVALID;
+    if (!is_tc_precision(opts->precision) || is_global_precision(opts->precision)) return TCGS_ERR_INVALID;
     if (!(opts->alpha_max > 0.f && opts->alpha_max <= 1.f)) return TCGS_ERR_INVALID;
     TcParams p = base_params(opts->precision, opacity);
     for (int v = 0; v < n_views; ++v) {
@@ -702,6 +843,7 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     p.alpha_max = opts->alpha_max;
     p.status = opts->device_status;
     p.tile_cull = opts->tile_cull;
+    p.early_cull = opts->early_cull;
     p.queue = queue;
     p.n_items = (uint32_t)n_items;
     p.counter = work_counter;
@@ -725,7 +867,7 @@ extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precis
     if (!valid_camera(cam) || !tile_ranges || !ids_sorted || !mean2d || !conic || !opacity || n_tiles < 0 ||
         max_n < 0 || (n_tiles > 0 && (!tiles || !beta_out)))
         return TCGS_ERR_INVALID;
-    if (precision != TCGS_TC_FP16 && precision != TCGS_TC_FP16_SPLIT) return TCGS_ERR_INVALID;
+    if (!is_tc_precision(precision)) return TCGS_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(mean2d) & 7) return TCGS_ERR_INVALID;
     if (n_tiles == 0 || max_n == 0) return TCGS_OK;
     if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;

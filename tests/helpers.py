@@ -19,14 +19,16 @@ def scene64(sc):
     return {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
 
 
-def oracle_frame(cam, sc, alpha_max=0.99, bg=(0, 0, 0)):
+def oracle_frame(cam, sc, alpha_max=0.99, bg=(0, 0, 0), render=True):
     """Oracle projection in FP64, then its outputs rounded to FP32: these FP32 values are the
-    common inputs of both sides for the binning and blending stages."""
+    common inputs of both sides for the binning and blending stages (and the oracle image unless
+    render is False)."""
     pr = oracle.project(cam, scene64(sc))
     inp = dict(mean2d=f32(pr["mean2d"]), conic=f32(pr["conic"]), depth=f32(pr["depth"]), radius=pr["radius"],
                rgb=f32(pr["rgb"]), opacity=f32(sc["opacity"]))
     b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"])
-    out = oracle.render(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["rgb"], bg=bg, alpha_max=alpha_max)
+    out = (oracle.render(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["rgb"], bg=bg, alpha_max=alpha_max)
+           if render else None)
     return pr, inp, b, out
 
 

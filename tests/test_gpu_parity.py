@@ -201,17 +201,21 @@ def test_render_tc_split_matches_oracle(tc, name, make, alpha_max):
 
 
 @pytest.mark.parametrize("name,make", SMALL)
-def test_render_tc_paper_padding_reports_error(tc, name, make):
-    """The paper's K = 8 layout (v0 / 3 three times): accuracy is reported, with a loose floor."""
+@pytest.mark.parametrize("precision", ["tc_fp16", "tc_tf32", "tc_fp8"])
+def test_render_tc_other_encodings_report_error(tc, name, make, precision):
+    """The paper's K = 8 layout (v0 / 3 three times), TF32 and the FP8 split: accuracy is
+    reported, with a loose floor."""
     cam, sc = make()
     _, inp, b, o = oracle_frame(cam, sc)
     g = gpu_inputs(inp, b)
-    out = tc.tcgs_render_fwd(cam, tc.render_opts("tc_fp16"), g["ranges"], g["ids"], g["mean2d"], g["conic"],
-                             g["opacity"], g["rgb"])
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    out = tc.tcgs_render_fwd(cam, tc.render_opts(precision, device_status=status), g["ranges"], g["ids"],
+                             g["mean2d"], g["conic"], g["opacity"], g["rgb"])
     torch.cuda.synchronize()
+    assert int(status.item()) == 0
     img = out["img"].cpu().numpy()
     p = psnr(img, o["img"])
-    print(f"\n[tc_fp16 paper padding] {name}: PSNR {p:.2f} dB, within 2e-3: "
+    print(f"\n[{precision}] {name}: PSNR {p:.2f} dB, within 2e-3: "
           f"{(np.abs(img - o['img']).max(axis=0) <= 2e-3).mean():.5f}")
     assert p >= 30.0
 
@@ -233,32 +237,88 @@ def test_render_outputs_empty_tiles_background(tc):
 
 # ------------------------------------------------------------------ Frag2Mat error bound (Appendix A)
 
-@pytest.mark.parametrize("precision,factor", [("tc_fp16", 1.0), ("tc_fp16_split", 2.0 ** -10)])
-def test_frag2mat_exponents_within_appendix_bound(tc, precision, factor):
+F16_MAX = 65504.0
+LOG2E = 1.0 / math.log(2.0)
+
+
+def _fp16_inputs_overflow(U, V):
+    """Per fragment: does the paper's K = 8 layout of u or v (log2 units, v0 / 3 in three slots)
+    leave the FP16 range (True), stay clearly inside it (False), or sit within 0.1 % of the edge
+    (None, not checked)?"""
+    Vp = np.abs(np.c_[V[:, :1] / 3, V[:, 1:]]) * LOG2E
+    Up = np.abs(U)
+    edge = 65520.0   # values from here up round to inf
+    over = (Up > edge).any(1)[:, None] | (Vp > edge).any(1)[None, :]
+    near = ((np.abs(Up - edge) < 1e-3 * edge).any(1)[:, None] | (np.abs(Vp - edge) < 1e-3 * edge).any(1)[None, :])
+    return over, near
+
+
+# precision -> (frame of u and v, bound on |beta_hat - beta| before the FP32 slack)
+F2M_MODES = {
+    "tc_fp16": ("local", lambda U, V, absum: f2m.paper_bound(absum)),
+    "tc_fp16_split": ("local", lambda U, V, absum: 2.0 ** -10 * f2m.paper_bound(absum)),
+    "tc_tf32": ("local", lambda U, V, absum: f2m.paper_bound(absum)),
+    "tc_fp8": ("local", lambda U, V, absum: f2m.fp8_split_bound(U, V)),
+    "tc_tf32_global": ("global", lambda U, V, absum: f2m.paper_bound(absum)),
+    "tc_fp16_global": ("global", lambda U, V, absum: f2m.paper_bound(absum)),
+}
+
+
+@pytest.mark.parametrize("precision", list(F2M_MODES))
+def test_frag2mat_exponents_within_appendix_bound(tc, precision):
+    frame, bound_of = F2M_MODES[precision]
     cam, sc = scenes.precision(P=30_000, width=240, height=120, seed=12)
-    _, inp, b, _ = oracle_frame(cam, sc)
+    _, inp, b, _ = oracle_frame(cam, sc, render=False)
     g = gpu_inputs(inp, b)
     gw, gh = oracle.grid(cam)
     lens = b["ranges"][:, 1] - b["ranges"][:, 0]
-    tiles = np.nonzero(lens > 0)[0][:24]
+    nz = np.nonzero(lens > 0)[0]
+    tiles = nz[np.linspace(0, len(nz) - 1, 24).astype(int)]   # spread over the image
     max_n = int(lens[tiles].max())
     beta = tc.tcgs_frag2mat_beta(cam, precision, g["ranges"], g["ids"], g["mean2d"], g["conic"], g["opacity"],
                                  tiles, max_n).cpu().numpy()
-    checked = 0
+    checked = culled_overflow = 0
     for k, t in enumerate(tiles):
         s, e = b["ranges"][t]
         ids = b["ids"][s:e]
-        _, _, bex, absum = f2m.local_products(t % gw, t // gw, inp["mean2d"][ids], inp["conic"][ids],
-                                              inp["opacity"][ids])
+        prod = f2m.local_products if frame == "local" else f2m.global_products
+        U, V, bex, absum = prod(t % gw, t // gw, inp["mean2d"][ids], inp["conic"][ids], inp["opacity"][ids])
         keep = bex >= -math.log(255.0)
         bh = beta[k, :, : e - s]
-        # paper bound (2 eps_H sum|u_i v_i|) scaled for the split layout, plus FP32 v-construction
-        # and accumulation slack (v is built from FP32 inputs in FP32)
-        bound = factor * f2m.paper_bound(absum) + 8 * 2.0 ** -24 * (absum + 8 * np.abs(bex)) + 1e-6
+        if precision == "tc_fp16_global":
+            over, near = _fp16_inputs_overflow(U, V)
+            # an input past the FP16 range gives -inf or NaN: the fragment is culled
+            ov = keep & over & ~near
+            assert not (bh[ov] >= -math.log(255.0)).any()
+            culled_overflow += int(ov.sum())
+            keep = keep & ~over & ~near
+        # FP32 v-construction and accumulation slack (v is built from FP32 inputs in FP32)
+        bound = bound_of(U, V, absum) + 8 * 2.0 ** -24 * (absum + 8 * np.abs(bex)) + 1e-6
+        if precision == "tc_fp8":
+            bound = bound + 32 * 2.0 ** -24 * absum   # 30 products accumulated
         err = np.abs(bh - bex)
         assert (err[keep] <= bound[keep]).all(), (precision, t, float((err - bound)[keep].max()))
         checked += int(keep.sum())
+    print(f"\n[frag2mat {precision}] fragments checked {checked}, culled by FP16 overflow {culled_overflow}")
     assert checked > 1000
+
+
+def test_global_coordinates_collapse_in_fp16(tc):
+    """Table 5: Frag2Mat without G2L.  Past 256 px FP16 overflows and the image collapses; TF32
+    stays finite but loses accuracy; G2L in FP16 is what keeps the image."""
+    cam, sc = scenes.precision(P=100_000, width=1024, height=512, seed=13)
+    _, inp, b, _ = oracle_frame(cam, sc, render=False)
+    g = gpu_inputs(inp, b)
+    imgs = {}
+    for prec in ["tc_fp16_split", "tc_fp16", "tc_fp16_global", "tc_tf32_global"]:
+        imgs[prec] = tc.tcgs_render_fwd(cam, tc.render_opts(prec), g["ranges"], g["ids"], g["mean2d"], g["conic"],
+                                        g["opacity"], g["rgb"])["img"].cpu().numpy()
+    ref = imgs["tc_fp16_split"]
+    p = {k: psnr(v, ref) for k, v in imgs.items() if k != "tc_fp16_split"}
+    print("\n[ablation, PSNR vs TC split] " + ", ".join(f"{k} {v:.2f} dB" for k, v in p.items()))
+    assert all(np.isfinite(v).all() for v in imgs.values())
+    assert p["tc_fp16_global"] < 20.0
+    assert p["tc_fp16"] > p["tc_tf32_global"] + 10.0
 
 
 # ------------------------------------------------------------------ backward

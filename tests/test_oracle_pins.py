@@ -419,6 +419,153 @@ def test_global_fp16_overflows_at_1920px():
     assert np.isinf(U.astype(np.float16)).any()
 
 
+def _format_values(exp_bits, frac_bits, bias, max_exp_field):
+    """Every finite non-negative value of a binary float format, built from its bit fields."""
+    vals = [0.0]
+    for f in range(1, 2 ** frac_bits):   # subnormals: 0.f x 2^(1 - bias)
+        vals.append(f / 2 ** frac_bits * 2.0 ** (1 - bias))
+    for e in range(1, max_exp_field + 1):
+        for f in range(2 ** frac_bits):
+            vals.append((1 + f / 2 ** frac_bits) * 2.0 ** (e - bias))
+    return np.array(sorted(vals))
+
+
+def test_e4m3_rounding_against_the_format_definition():
+    # e4m3: exponent field 1..15 normal except the all-ones pattern 1111.111 (NaN), so the
+    # largest finite value is 1.110 x 2^8 = 448
+    vals = _format_values(4, 3, 7, 15)[:-1]
+    assert vals[-1] == 448.0 and vals[1] == 2.0 ** -9 and len(vals) == 127
+    assert np.array_equal(f2m.round_e4m3(vals), vals)
+    assert np.array_equal(f2m.round_e4m3(-vals), -vals)
+    mids = 0.5 * (vals[1:] + vals[:-1])
+    r = f2m.round_e4m3(mids)
+    # a midpoint goes to the neighbour whose last fraction bit is 0 (ties to even)
+    lo, hi = vals[:-1], vals[1:]
+    even_lo = np.array([(round(v / 2.0 ** (max(math.floor(math.log2(v)), -6) - 3)) % 2 == 0) if v > 0 else True
+                        for v in lo])
+    assert np.array_equal(r, np.where(even_lo, lo, hi))
+    rng = np.random.default_rng(30)
+    x = rng.uniform(0, 460, 20000) * 2.0 ** rng.integers(-12, 1, 20000)
+    r = f2m.round_e4m3(x)
+    nearest = vals[np.abs(x[:, None] - vals[None, :]).argmin(1)]
+    ok = np.abs(r - x) <= np.abs(nearest - x) + 0.0
+    assert ok.all()
+    assert f2m.round_e4m3(1e6) == 448.0   # saturation
+
+
+def test_tf32_rounding_against_the_format_definition():
+    rng = np.random.default_rng(31)
+    x = rng.uniform(1, 2, 20000)
+    r = f2m.round_tf32(x)
+    grid = 1 + np.arange(2 ** 10 + 1) / 2 ** 10   # TF32 values in [1, 2]
+    idx = np.abs(x[:, None] - grid[None, :]).argmin(1)
+    assert np.array_equal(r, grid[idx])
+    assert f2m.round_tf32(1 + 2.0 ** -11) == 1 + 2.0 ** -10      # ties away from zero
+    assert f2m.round_tf32(-(1 + 2.0 ** -11)) == -(1 + 2.0 ** -10)
+    assert np.array_equal(f2m.round_tf32(x * 2.0 ** 40), r * 2.0 ** 40)
+
+
+def test_fp8_split_of_tile_pixel_vectors_is_exact():
+    """Every G2L pixel vector, column-scaled, is the sum of two e4m3 numbers: u is carried
+    exactly by the FP8 encoding, so all of its error comes from v."""
+    dx, dy = f2m.tile_pixels_local()
+    U = f2m.pixel_vectors(dx, dy) * 2.0 ** -np.array(f2m.FP8_COLUMN_EXP)
+    hi = f2m.round_e4m3(U)
+    lo = f2m.round_e4m3(U - hi)
+    assert np.array_equal(hi + lo, U)
+    assert np.abs(U).min() >= 2.0 ** -8   # (dx, dy never 0) every part at or above the subnormal grid
+
+
+def _reachable_gaussians(rng, n):
+    """Tile-local Gaussians that can reach alpha >= 1/255 in a tile: Q with eigenvalues in
+    [1e-4, 1 / 0.3] (the 0.3 px^2 dilation), opacity in [1/255, 1], and Q-distance of the local
+    mean at most sqrt(2 ln(255 o)) + 7.5 sqrt(2) sqrt(lambda_max(Q)) (the reach of the tile), with
+    a share of samples on the extremes."""
+    lam = np.exp(rng.uniform(np.log(1e-4), np.log(1 / 0.3), (n, 2)))
+    lam[: n // 4, :] = 1 / 0.3
+    th = rng.uniform(0, np.pi, n)
+    c, s = np.cos(th), np.sin(th)
+    Q11 = lam[:, 0] * c * c + lam[:, 1] * s * s
+    Q22 = lam[:, 0] * s * s + lam[:, 1] * c * c
+    Q12 = (lam[:, 0] - lam[:, 1]) * c * s
+    o = np.exp(rng.uniform(np.log(1 / 255), 0, n))
+    o[: n // 4] = 1.0
+    lmax = lam.max(1)
+    reach = np.sqrt(2 * np.log(255 * o)) + 7.5 * np.sqrt(2) * np.sqrt(lmax)
+    # a point at Q-distance `reach` in a random direction: mu = reach * L^-T w, |w| = 1
+    phi = rng.uniform(0, 2 * np.pi, n)
+    w = np.stack([np.cos(phi), np.sin(phi)], 1)
+    frac = np.where(np.arange(n) < n // 2, 1.0, rng.uniform(0, 1, n))
+    mu = np.empty((n, 2))
+    for i in range(n):
+        Q = np.array([[Q11[i], Q12[i]], [Q12[i], Q22[i]]])
+        Lc = np.linalg.cholesky(Q)
+        mu[i] = np.linalg.solve(Lc.T, w[i]) * reach[i] * frac[i]
+    return mu, np.stack([Q11, Q12, Q22], 1), o
+
+
+def test_fp8_column_scales_keep_reachable_v_in_range():
+    rng = np.random.default_rng(32)
+    mu, conic, o = _reachable_gaussians(rng, 4000)
+    V = f2m.gaussian_vectors(mu, conic, o) / math.log(2.0)        # log2 units, as encoded
+    Vs = V * 2.0 ** np.array(f2m.FP8_COLUMN_EXP)
+    assert np.abs(Vs).max() < f2m.E4M3_MAX
+
+
+def test_fp8_split_bound_holds_by_emulation():
+    rng = np.random.default_rng(33)
+    mu, conic, o = _reachable_gaussians(rng, 3000)
+    dx, dy = f2m.tile_pixels_local()
+    U = f2m.pixel_vectors(dx, dy)
+    V = f2m.gaussian_vectors(mu, conic, o) / math.log(2.0)
+    exact = U @ V.T
+    got = f2m.fp8_split(U, V)
+    bound = f2m.fp8_split_bound(U, V, log2_scale=True)
+    err = np.abs(got - exact)
+    assert (err <= bound).all(), float((err - bound).max())
+    # the bound is not vacuous (some fragment comes within a factor 5 of it), and the split is far
+    # better than a single e4m3 rounding of v
+    assert (err / bound).max() > 0.2
+    sc = 2.0 ** np.array(f2m.FP8_COLUMN_EXP)
+    one_term = (U / sc) @ f2m.round_e4m3(V * sc).T
+    assert np.abs(one_term - exact).max() > 100 * err.max()
+
+
+def test_appendix_bound_holds_for_tf32_in_global_coordinates():
+    """Frag2Mat without G2L on TF32 inputs (Table 5): the Appendix A bound still holds, but in
+    global coordinates sum |u_i v_i| is orders of magnitude larger than |beta|."""
+    rng = np.random.default_rng(34)
+    n = 200
+    mean2d = np.c_[rng.uniform(1700, 1800, n), rng.uniform(900, 1000, n)]
+    mu, conic, o = _reachable_gaussians(rng, n)
+    tx, ty = 1750 // 16, 950 // 16
+    U, V, beta, absum = f2m.global_products(tx, ty, f2m.tile_centre(tx, ty)[None, :] + mu, conic, o)
+    got = f2m.round_tf32(U) @ f2m.round_tf32(V).T
+    assert (np.abs(got - beta) <= f2m.paper_bound(absum)).all()
+    # same Gaussians in the tile's local frame: the bound shrinks by orders of magnitude
+    _, _, beta_l, absum_l = f2m.local_products(tx, ty, f2m.tile_centre(tx, ty)[None, :] + mu, conic, o)
+    np.testing.assert_allclose(beta_l, beta, atol=1e-6 * np.abs(absum).max())
+    assert np.median(absum / absum_l) > 1e3
+
+
+def test_global_fp16_overflow_culls():
+    """Past 256 px, u's quadratic terms overflow FP16 to +inf; with sigma11, sigma22 > 0 the
+    exponent is then -inf or NaN, which the EarlyCull comparison rejects: the fragment is dropped."""
+    rng = np.random.default_rng(35)
+    mu, conic, o = _reachable_gaussians(rng, 200)
+    tx, ty = 40, 20
+    c = f2m.tile_centre(tx, ty)
+    U, V, beta, _ = f2m.global_products(tx, ty, c[None, :] + mu, conic, o)
+    # the paper's K = 8 layout of both operands
+    Up = np.c_[U[:, :1], U[:, :1], U[:, :1], U[:, 1:]].astype(np.float16).astype(np.float64)
+    Vp = np.c_[V[:, :1] / 3, V[:, :1] / 3, V[:, :1] / 3, V[:, 1:]].astype(np.float16).astype(np.float64)
+    assert np.isinf(Up).any(axis=1).all()
+    with np.errstate(invalid="ignore", over="ignore"):
+        bh = Up @ Vp.T
+    assert not (bh >= -math.log(255.0)).any()
+    assert (np.isnan(bh) | (bh == -np.inf)).all()
+
+
 def test_constants_match_paper():
     assert abs(f2m.EPS_H - GOLD["eps_H"]["value"]) < 5e-7
     assert abs(f2m.EPS_F - GOLD["eps_F"]["value"]) < 5e-10
