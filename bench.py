@@ -366,6 +366,86 @@ def bench_ablation(r, dsc, flush, img32, oracle_img=None, mask=None, reps=10, wa
     return out
 
 
+def time_frames(r, dsc, precision, steps, warmup, use_graph, flush, stream):
+    """Frames of renderer r (project -> bin_sort -> render), one CUDA graph per stage so each stage
+    keeps its own events; L2 flushed before every timed frame, outside the events.  Returns the
+    frame times and the per-stage times (ms)."""
+    import torch
+    fns = [lambda: r.project(dsc), lambda: r.bin_sort(), lambda: r.render(dsc["opacity"], precision)]
+    if use_graph:
+        for f in fns:
+            f()
+        torch.cuda.synchronize()
+        graphs = []
+        for f in fns:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                f()
+            graphs.append(g)
+        run = [g.replay for g in graphs]
+    else:
+        run = fns
+    for _ in range(warmup):
+        for f in run:
+            f()
+    torch.cuda.synchronize()
+    per_stage = [[] for _ in run]
+    total = []
+    for _ in range(steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(run) + 1)]
+        ev[0].record(stream)
+        for i, f in enumerate(run):
+            f()
+            ev[i + 1].record(stream)
+        ev[-1].synchronize()
+        for i in range(len(run)):
+            per_stage[i].append(ev[i].elapsed_time(ev[i + 1]))
+        total.append(ev[0].elapsed_time(ev[-1]))
+    return total, per_stage
+
+
+def bench_tight_radius(cam, sc, dsc, dev, flush, with_oracle=True, reps=20, warmup=5):
+    """The same frame binned with the opacity-aware coverage square (Gaussians cover only the
+    tiles where alpha >= 1/255 is possible): splats and stage times, and the image against the
+    oracle run with the same coverage on a sample of tiles."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    P = len(sc["opacity"])
+    pr = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], dsc["sh_degree"],
+                         opacity=dsc["opacity"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    del pr
+    r = tc.Renderer(cam, P, n + 1024, device=dev, tight_radius=True)
+    tot, stg = time_frames(r, dsc, "tc_fp16_split", reps, warmup, True, flush, torch.cuda.current_stream(dev))
+    ms = dict(zip(["project", "bin_sort", "render_fwd"], [statistics.mean(x) for x in stg]))
+    r.frame(dsc, precision="tc_fp16_split")
+    torch.cuda.synchronize()
+    out = {"splats": n, "stages_ms": ms, "frame_ms": statistics.mean(tot),
+           "frames_per_s": 1000.0 / statistics.mean(tot)}
+    if with_oracle:
+        import oracle
+        s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+        po = oracle.project(cam, s64, tight_radius=True)
+        b = oracle.bin_sort(cam, po["mean2d"], po["radius"], po["depth"])
+        gw, gh = oracle.grid(cam)
+        tiles = np.random.default_rng(7).choice(gw * gh, (gw * gh) // 8, replace=False)
+        o = oracle.render(cam, b, po["mean2d"], po["conic"], s64["opacity"], po["rgb"], tiles=tiles, margins=False)
+        H, W = cam["height"], cam["width"]
+        mask = np.zeros((H, W), bool)
+        for t in tiles:
+            ty, tx = divmod(int(t), gw)
+            mask[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
+        d = (r.out["img"].cpu().numpy().astype(np.float64) - o["img"])[:, mask]
+        mse = float(np.mean(d ** 2))
+        out["oracle_splats"] = int(b["n"])
+        out["psnr_vs_oracle_db"] = 10 * math.log10(1 / mse) if mse > 0 else None
+        out["within_2e-3_vs_oracle"] = float((np.abs(d).max(axis=0) <= 2e-3).mean())
+        out["oracle_pixels_compared"] = int(mask.sum())
+    del r
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_tcgs(args):
@@ -410,55 +490,16 @@ def run_tcgs(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (126 MB)
     stream = torch.cuda.current_stream(dev)
 
-    def stage_fns(precision):
-        return [lambda: r.project(dsc), lambda: r.bin_sort(), lambda: r.render(dsc["opacity"], precision)]
-
-    def time_frames(precision, steps, warmup, use_graph):
-        fns = stage_fns(precision)
-        graphs = None
-        if use_graph:
-            # one CUDA graph per stage so each stage keeps its own events
-            for f in fns:
-                f()
-            torch.cuda.synchronize()
-            graphs = []
-            for f in fns:
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g):
-                    f()
-                graphs.append(g)
-            run = [g.replay for g in graphs]
-        else:
-            run = fns
-        for _ in range(warmup):
-            for f in run:
-                f()
-        torch.cuda.synchronize()
-        per_stage = [[] for _ in run]
-        total = []
-        for _ in range(steps):
-            flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(run) + 1)]
-            ev[0].record(stream)
-            for i, f in enumerate(run):
-                f()
-                ev[i + 1].record(stream)
-            ev[-1].synchronize()
-            for i in range(len(run)):
-                per_stage[i].append(ev[i].elapsed_time(ev[i + 1]))
-            total.append(ev[0].elapsed_time(ev[-1]))
-        return total, per_stage
-
     use_graph = not args.no_graph
     # --- FP32 comparison path
-    tot32, st32 = time_frames("fp32", args.steps, args.warmup, use_graph)
+    tot32, st32 = time_frames(r, dsc, "fp32", args.steps, args.warmup, use_graph, flush, stream)
     # --- headline path, with clocks sampled during the timed region
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = lib.tcgs_kernel_launches()
     with ClockSampler(local) as clk:
-        tot, stg = time_frames(args.precision, args.steps, args.warmup, use_graph)
+        tot, stg = time_frames(r, dsc, args.precision, args.steps, args.warmup, use_graph, flush, stream)
     launches_total = lib.tcgs_kernel_launches() - l0
     torch.cuda.synchronize()
     # launches per frame, counted by the library on one eager frame (graphs replay the same kernels)
@@ -529,9 +570,10 @@ def run_tcgs(args):
             acc[f"within_2e-3_{name}"] = float((np.abs(d).max(axis=0) <= 2e-3).mean())
             acc[f"max_abs_{name}"] = float(np.abs(d).max())
         acc["oracle_pixels_compared"] = int(mask.sum())
-    ablation = None
+    ablation = tight = None
     if not args.no_extras:
         ablation = bench_ablation(r, dsc, flush, img_fp32, oimg, mask)
+        tight = bench_tight_radius(cam, sc, dsc, dev, flush, with_oracle=not args.no_cpu_baseline)
 
     # --- roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -598,6 +640,7 @@ def run_tcgs(args):
         "clocks": clocks,
         "workloads": extras,
         "ablation": ablation,
+        "tight_radius": tight,
     }
     print(json.dumps(line))
     if world > 1:

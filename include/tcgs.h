@@ -116,12 +116,16 @@ TCGS_API uint64_t tcgs_kernel_launches(void);
  * Preprocess (Sec. 3.1, Eq. 2): EWA projection of P 3D Gaussians.
  *   Sigma = R(q) diag(s)^2 R(q)^T, t = W mu, J = d(mean2d)/d(t) at t with x/z, y/z
  *   clamped to +-1.3 tan_fov, Sigma' = J W Sigma W^T J^T + 0.3 I (low-pass dilation),
- *   conic = Sigma'^-1 = (sigma11, sigma12, sigma22), radius = ceil(3 sqrt(lambda_max)),
- *   lambda_max = m + sqrt(max(0.1, m^2 - det)), m = (a + c) / 2.
+ *   conic = Sigma'^-1 = (sigma11, sigma12, sigma22), radius = half-width of the coverage square
+ *   (below), lambda_max = m + sqrt(max(0.1, m^2 - det)), m = (a + c) / 2.
  *   Colour = sum_k sh[k] Y_k(dir) + 0.5 clamped at 0, dir = (mu - campos) / |mu - campos|,
  *   real SH up to degree 3 (3DGS convention).
+ * Coverage square: with opacity == NULL, the 3-sigma square of official 3DGS,
+ *   radius = ceil(3 sqrt(lambda_max)); with opacity [P] (post-sigmoid), the opacity-aware square
+ *   that bounds the ellipse where alpha = o exp(-q/2) >= 1/255 (Eq. 5),
+ *   radius = ceil(sqrt(2 ln(255 o) lambda_max)), and Gaussians with o <= 1/255 are culled.
  * In:  means3 [P,3]; scales [P,3] (standard deviations, > 0); quats [P,4] (w,x,y,z, any
- *      non-zero norm); sh [P, (sh_degree+1)^2, 3]; 0 <= sh_degree <= 3.
+ *      non-zero norm); sh [P, (sh_degree+1)^2, 3]; 0 <= sh_degree <= 3; opacity [P] or NULL.
  * Out: mean2d [P,2]; conic [P,3]; depth [P] (camera Z); radius [P] int32 (0 = culled: behind the
  *      near plane, degenerate, or touching no tile); rgb [P,3]; tiles_touched [P] uint32.
  *      Culled Gaussians get zeros in every output.
@@ -129,7 +133,7 @@ TCGS_API uint64_t tcgs_kernel_launches(void);
  */
 TCGS_API tcgs_status tcgs_project(const tcgs_camera* cam /* host */, int32_t P, int32_t sh_degree,
                          const float* means3, const float* scales, const float* quats, const float* sh,
-                         float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
+                         const float* opacity /* nullable */, float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
                          uint32_t* tiles_touched, tcgs_stream stream);
 
 /* Bytes of device workspace tcgs_bin_sort needs (a pure host function). */

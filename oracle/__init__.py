@@ -66,7 +66,7 @@ def _L():
             cam = P(Camera)
             lib.orc_sh_basis.argtypes = [ctypes.c_int, P(d), P(d)]
             lib.orc_quat_to_rot.argtypes = [P(d), P(d)]
-            lib.orc_project.argtypes = [cam, ctypes.c_int, ctypes.c_int] + [P(d)] * 5 + \
+            lib.orc_project.argtypes = [cam, ctypes.c_int, ctypes.c_int] + [P(d)] * 5 + [ctypes.c_int] + \
                 [P(d), P(d), P(d), P(i32), P(d), P(i32), P(d)]
             lib.orc_count_splats.argtypes = [cam, ctypes.c_int, P(d), P(i32)]
             lib.orc_count_splats.restype = i64
@@ -108,8 +108,9 @@ def quat_to_rot(q) -> np.ndarray:
     return R.reshape(3, 3)
 
 
-def project(cam: dict, scene: dict) -> dict:
-    """Preprocess stage in FP64 (Sec. 3.1, Eq. 2)."""
+def project(cam: dict, scene: dict, tight_radius: bool = False) -> dict:
+    """Preprocess stage in FP64 (Sec. 3.1, Eq. 2).  tight_radius: the coverage square bounds the
+    ellipse where alpha >= 1/255 (opacity-aware) instead of the 3-sigma square."""
     c = camera(cam)
     means3 = _f64(scene["means3"]); P = means3.shape[0]
     deg = int(scene["sh_degree"])
@@ -119,7 +120,7 @@ def project(cam: dict, scene: dict) -> dict:
     d = ctypes.c_double
     _L().orc_project(ctypes.byref(c), P, deg, _p(means3, d), _p(_f64(scene["scales"]), d),
                      _p(_f64(scene["quats"]), d), _p(_f64(scene["opacity"]), d), _p(_f64(scene["sh"]), d),
-                     _p(out["mean2d"], d), _p(out["conic"], d), _p(out["depth"], d),
+                     int(bool(tight_radius)), _p(out["mean2d"], d), _p(out["conic"], d), _p(out["depth"], d),
                      _p(out["radius"], ctypes.c_int32), _p(out["rgb"], d),
                      _p(out["tiles_touched"], ctypes.c_int32), _p(out["cov2d"], d))
     return out

@@ -116,14 +116,18 @@ static int64_t tile_rect(const orc_camera* cam, double mx, double my, int32_t r,
 /* Sigma = R S S^T R^T with S = diag(scale); conic = (Sigma')^{-1} stored as  */
 /* (sigma11, sigma12, sigma22) in the notation of Sec. 4.2.                   */
 /* cov2d_out (nullable) receives (a, b, c) of Sigma' after dilation.          */
+/* Coverage radius: tight_radius = 0 gives the 3-sigma square of official    */
+/* 3DGS, r = ceil(3 sqrt(lambda_max)); tight_radius = 1 the square bounding  */
+/* the ellipse where alpha >= 1/255 (Eq. 5): o exp(-q/2) >= 1/255 iff        */
+/* q <= 2 ln(255 o), so r = ceil(sqrt(2 ln(255 o) lambda_max)); a Gaussian   */
+/* with o <= 1/255 reaches no pixel and is culled.                            */
 /* ------------------------------------------------------------------------ */
 void orc_project(const orc_camera* cam, int P, int sh_degree,
                  const double* means3, const double* scales, const double* quats,
-                 const double* opacity, const double* sh,
+                 const double* opacity, const double* sh, int tight_radius,
                  double* mean2d, double* conic, double* depth, int32_t* radius,
                  double* rgb, int32_t* tiles_touched, double* cov2d_out)
 {
-    (void)opacity;
     const double* V = cam->viewmat;
     int K = (sh_degree + 1) * (sh_degree + 1);
     for (int g = 0; g < P; ++g) {
@@ -184,7 +188,12 @@ void orc_project(const orc_camera* cam, int P, int sh_degree,
         double mid = 0.5 * (a + c);
         double lam1 = mid + sqrt(fmax(0.1, mid * mid - det));
         double lam2 = mid - sqrt(fmax(0.1, mid * mid - det));
-        int32_t r = (int32_t)ceil(3.0 * sqrt(fmax(lam1, lam2)));
+        double reach2 = 9.0;   /* squared reach in units of sigma */
+        if (tight_radius) {
+            reach2 = 2.0 * log(255.0 * opacity[g]);
+            if (!(reach2 > 0.0)) continue;
+        }
+        int32_t r = (int32_t)ceil(sqrt(reach2 * fmax(lam1, lam2)));
         double mx = cam->fx * t[0] / t[2] + cam->cx;
         double my = cam->fy * t[1] / t[2] + cam->cy;
         int x0, x1, y0, y1;

@@ -91,7 +91,8 @@ def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=None, tile
 
 # ---------------------------------------------------------------- one-to-one C ABI wrappers
 
-def tcgs_project(cam, means3, scales, quats, sh, sh_degree, out=None, stream=None) -> dict:
+def tcgs_project(cam, means3, scales, quats, sh, sh_degree, out=None, stream=None, opacity=None) -> dict:
+    """opacity: None for the 3-sigma coverage square, or the opacities for the opacity-aware one."""
     c = _cam(cam)
     P = means3.shape[0]
     dev = means3.device
@@ -102,7 +103,8 @@ def tcgs_project(cam, means3, scales, quats, sh, sh_degree, out=None, stream=Non
     f = torch.float32
     check("tcgs_project", _L().tcgs_project(
         ctypes.byref(c), P, int(sh_degree), _ptr(means3, f, "means3"), _ptr(scales, f, "scales"),
-        _ptr(quats, f, "quats"), _ptr(sh, f, "sh"), _ptr(out["mean2d"], f), _ptr(out["conic"], f),
+        _ptr(quats, f, "quats"), _ptr(sh, f, "sh"), _ptr(opacity, f, "opacity") if opacity is not None else None,
+        _ptr(out["mean2d"], f), _ptr(out["conic"], f),
         _ptr(out["depth"], f), _ptr(out["radius"], torch.int32), _ptr(out["rgb"], f),
         _ptr(out["tiles_touched"], torch.int32), _stream(stream)))
     return out
@@ -315,8 +317,10 @@ class Renderer:
     """Preallocated buffers for one camera, scene size and splat capacity; ``frame`` runs
     project -> bin_sort -> render_fwd on the current stream with no host synchronisation."""
 
-    def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False):
+    def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False, tight_radius: bool = False):
+        """tight_radius: bin with the opacity-aware coverage square instead of the 3-sigma one."""
         self.cam = _cam(cam)
+        self.tight_radius = bool(tight_radius)
         self.P, self.capacity = int(P), int(capacity)
         dev = torch.device(device)
         gw, gh = grid(self.cam)
@@ -339,7 +343,8 @@ class Renderer:
 
     def project(self, scene: dict, stream=None):
         return tcgs_project(self.cam, scene["means3"], scene["scales"], scene["quats"], scene["sh"],
-                            scene["sh_degree"], out=self.proj, stream=stream)
+                            scene["sh_degree"], out=self.proj, stream=stream,
+                            opacity=scene["opacity"] if self.tight_radius else None)
 
     def bin_sort(self, stream=None):
         return tcgs_bin_sort(self.cam, self.proj["mean2d"], self.proj["radius"], self.proj["depth"], self.capacity,

@@ -40,7 +40,8 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
 
 __global__ void __launch_bounds__(256) k_project(DevCamera cam, int P, int deg, const float* __restrict__ means3,
                                                  const float* __restrict__ scales, const float* __restrict__ quats,
-                                                 const float* __restrict__ sh, float* __restrict__ mean2d,
+                                                 const float* __restrict__ sh, const float* __restrict__ opacity,
+                                                 float* __restrict__ mean2d,
                                                  float* __restrict__ conic, float* __restrict__ depth,
                                                  int32_t* __restrict__ radius, float* __restrict__ rgb,
                                                  uint32_t* __restrict__ tiles_touched) {
@@ -96,10 +97,13 @@ __global__ void __launch_bounds__(256) k_project(DevCamera cam, int P, int deg, 
         float b = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
         float c = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2] + 0.3f;
         float det = a * c - b * b;
-        if (det > 0.f) {
+        // squared reach in units of sigma: 9 for the 3-sigma square, 2 ln(255 o) for the square
+        // bounding the ellipse where alpha >= 1/255 (Eq. 5); o <= 1/255 reaches no pixel
+        const float reach2 = opacity ? 2.f * logf(255.f * opacity[g]) : 9.f;
+        if (det > 0.f && reach2 > 0.f) {
             float mid = 0.5f * (a + c);
             float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-            float rf = ceilf(3.f * sqrtf(lam));
+            float rf = ceilf(sqrtf(reach2 * lam));
             int32_t r = rf < 1.0e9f ? (int32_t)rf : 1000000000;
             float mx = cam.fx * tx * iz + cam.cx;
             float my = cam.fy * ty * iz + cam.cy;
@@ -151,7 +155,8 @@ __global__ void __launch_bounds__(256) k_project(DevCamera cam, int P, int deg, 
 }  // namespace tcgs
 
 extern "C" tcgs_status tcgs_project(const tcgs_camera* cam, int32_t P, int32_t sh_degree, const float* means3,
-                                    const float* scales, const float* quats, const float* sh, float* mean2d,
+                                    const float* scales, const float* quats, const float* sh,
+                                    const float* opacity, float* mean2d,
                                     float* conic, float* depth, int32_t* radius, float* rgb,
                                     uint32_t* tiles_touched, tcgs_stream stream) {
     using namespace tcgs;
@@ -165,7 +170,7 @@ extern "C" tcgs_status tcgs_project(const tcgs_camera* cam, int32_t P, int32_t s
     DevCamera dc = make_dev_camera(*cam);
     int threads = 256;
     int blocks = (P + threads - 1) / threads;
-    k_project<<<blocks, threads, 0, (cudaStream_t)stream>>>(dc, P, sh_degree, means3, scales, quats, sh, mean2d,
+    k_project<<<blocks, threads, 0, (cudaStream_t)stream>>>(dc, P, sh_degree, means3, scales, quats, sh, opacity, mean2d,
                                                            conic, depth, radius, rgb, tiles_touched);
     count_launches(1);
     TCGS_CHECK_LAUNCH();

@@ -59,11 +59,11 @@ def test_invalid_arguments_rejected_on_host(lib):
     cam = _lib.tcgs_camera()
     cam.width, cam.height, cam.fx, cam.fy = 0, 10, 1.0, 1.0   # invalid width
     V = None
-    assert lib.tcgs_project(ctypes.byref(cam), 10, 0, *([V] * 10), None) == _lib.TCGS_ERR_INVALID
+    assert lib.tcgs_project(ctypes.byref(cam), 10, 0, *([V] * 11), None) == _lib.TCGS_ERR_INVALID
     cam.width = 16
-    assert lib.tcgs_project(ctypes.byref(cam), 10, 4, *([V] * 10), None) == _lib.TCGS_ERR_INVALID  # degree > 3
-    assert lib.tcgs_project(ctypes.byref(cam), 10, 0, *([V] * 10), None) == _lib.TCGS_ERR_INVALID  # null arrays
-    assert lib.tcgs_project(ctypes.byref(cam), 0, 0, *([V] * 10), None) == _lib.TCGS_OK             # empty: no-op
+    assert lib.tcgs_project(ctypes.byref(cam), 10, 4, *([V] * 11), None) == _lib.TCGS_ERR_INVALID  # degree > 3
+    assert lib.tcgs_project(ctypes.byref(cam), 10, 0, *([V] * 11), None) == _lib.TCGS_ERR_INVALID  # null arrays
+    assert lib.tcgs_project(ctypes.byref(cam), 0, 0, *([V] * 11), None) == _lib.TCGS_OK             # empty: no-op
     opts = _lib.tcgs_render_opts()
     opts.precision, opts.alpha_max = 9, 0.99
     assert lib.tcgs_render_fwd(ctypes.byref(cam), ctypes.byref(opts), *([V] * 10), None) == _lib.TCGS_ERR_INVALID

@@ -47,11 +47,13 @@ SMALL = [
 # ------------------------------------------------------------------ projection
 
 @pytest.mark.parametrize("name,make", SMALL)
-def test_project_matches_oracle(tc, name, make):
+@pytest.mark.parametrize("tight", [False, True])
+def test_project_matches_oracle(tc, name, make, tight):
     cam, sc = make()
-    pr = oracle.project(cam, scene64(sc))
+    pr = oracle.project(cam, scene64(sc), tight_radius=tight)
     dsc = {k: to_torch(v, DEV) for k, v in sc.items() if isinstance(v, np.ndarray)}
-    out = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], sc["sh_degree"])
+    out = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], sc["sh_degree"],
+                          opacity=dsc["opacity"] if tight else None)
     torch.cuda.synchronize()
     g = {k: v.cpu().numpy() for k, v in out.items()}
     vis_o = pr["radius"] > 0
@@ -71,6 +73,35 @@ def test_project_matches_oracle(tc, name, make):
     rad_diff = g["radius"][both] != pr["radius"][both]
     assert rad_diff.mean() < 1e-3
     assert (np.abs(g["radius"][both] - pr["radius"][both]) <= 1).all()
+
+
+def test_tight_radius_render_matches_oracle(tc):
+    """Opacity-aware coverage: GPU project -> bin_sort -> TC render against the oracle on the
+    same (FP32-rounded) projection, and fewer splats than the 3-sigma square where opacities are low."""
+    cam, sc = scenes.precision(P=30_000, width=240, height=120, seed=12)
+    dsc = tc.scene_to_device(sc, DEV)
+    pr = oracle.project(cam, scene64(sc), tight_radius=True)
+    inp = dict(mean2d=f32(pr["mean2d"]), conic=f32(pr["conic"]), depth=f32(pr["depth"]), radius=pr["radius"],
+               rgb=f32(pr["rgb"]), opacity=f32(sc["opacity"]))
+    b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"])
+    o = oracle.render(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["rgb"])
+    g = gpu_inputs(inp, b)
+    out = tc.tcgs_render_fwd(cam, tc.render_opts("tc_fp16_split"), g["ranges"], g["ids"], g["mean2d"], g["conic"],
+                             g["opacity"], g["rgb"])
+    torch.cuda.synchronize()
+    img = out["img"].cpu().numpy()
+    assert psnr(img, o["img"]) >= 50.0
+    assert (np.abs(img - o["img"]).max(axis=0) <= 2e-3).mean() >= 0.999
+    # the GPU's own projection bins to the oracle's splat count up to radius rounding edges
+    r = tc.Renderer(cam, len(sc["opacity"]), b["n"] + 4096, tight_radius=True)
+    r.project(dsc)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    n_gpu = int(r.bins["n_splats"].item())
+    assert abs(n_gpu - b["n"]) <= max(20, 1e-3 * b["n"])
+    p3 = oracle.project(cam, scene64(sc))
+    wide = oracle.bin_sort(cam, f32(p3["mean2d"]), p3["radius"], f32(p3["depth"]))
+    print(f"\n[tight radius] splats {b['n']} (3-sigma square: {wide['n']})")
 
 
 # ------------------------------------------------------------------ binning (bit exact)

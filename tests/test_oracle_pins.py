@@ -346,6 +346,46 @@ def test_tiled_equals_untiled_bruteforce(seed, bg):
     assert np.array_equal(out["n_contrib"], bf["n_contrib"])
 
 
+def test_tight_radius_closed_form_and_opacity_cull():
+    f, z, s = 300.0, 5.0, 0.04
+    cam = scenes.pinhole(320, 240, fx=f)
+    var = (f * s / z) ** 2 + 0.3
+    for o in [0.9, 0.05, 1.5 / 255]:
+        sc = make_scene([0, 0, z], [s, s, s], [1, 0, 0, 0], [o], [[0.2, 0.4, 0.6]])
+        pr = oracle.project(cam, sc, tight_radius=True)
+        assert pr["radius"][0] == math.ceil(math.sqrt(2 * math.log(255 * o) * (var + math.sqrt(0.1))))
+    sc = make_scene([0, 0, z], [s, s, s], [1, 0, 0, 0], [0.999 / 255], [[0.2, 0.4, 0.6]])
+    assert oracle.project(cam, sc, tight_radius=True)["radius"][0] == 0      # reaches no pixel
+    assert oracle.project(cam, sc)["radius"][0] > 0                           # the 3-sigma square keeps it
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_tight_radius_tiled_equals_untiled_without_membership(seed):
+    """With the opacity-aware square, every pixel where alpha >= 1/255 lies in a covered tile, so
+    the tiled render equals Algorithm 1 over all Gaussians at every pixel; the 3-sigma square cuts
+    opaque Gaussians off (o exp(-9/2) > 1/255 when o > 0.36) and does not."""
+    cam, sc = scenes.plain_forward(P=200, width=56, height=40, seed=seed)
+    sc = scene_arrays(sc)
+    sc["opacity"] = np.where(np.arange(200) % 2 == 0, 0.97, sc["opacity"])   # many opaque Gaussians
+    sc["scales"] = sc["scales"] * 4                                          # splats of several pixels
+    op = sc["opacity"]
+    proj = {tight: oracle.project(cam, sc, tight_radius=tight) for tight in (True, False)}
+    # every Gaussian either square keeps, each at every pixel (one left out by both has alpha < 1/255
+    # at every pixel, or fails the near-plane or determinant test)
+    kept_t = proj[True]["radius"] > 0
+    src = {k: np.where(kept_t.reshape(-1, *[1] * (proj[True][k].ndim - 1)), proj[True][k], proj[False][k])
+           for k in ("mean2d", "conic", "depth", "rgb")}
+    everywhere = np.where(kept_t | (proj[False]["radius"] > 0), 10 ** 6, 0).astype(np.int32)
+    bf = oracle.render_bruteforce(cam, src["mean2d"], everywhere, src["depth"], src["conic"], op, src["rgb"])
+    err = {}
+    for tight, pr in proj.items():
+        b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+        out = oracle.render(cam, b, pr["mean2d"], pr["conic"], op, pr["rgb"])
+        err[tight] = (np.abs(out["img"] - bf["img"]).max(), np.abs(out["T"] - bf["T"]).max())
+    assert err[True][0] <= 1e-12 and err[True][1] <= 1e-12
+    assert err[False][0] > 1e-4
+
+
 def test_fragment_counts_consistent():
     cam, sc = scenes.plain_forward(P=300, width=64, height=64, seed=5)
     pr, b, out = _render_scene(cam, scene_arrays(sc))
