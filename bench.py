@@ -220,13 +220,20 @@ def bench_differentiation(dev, flush):
     bwd_ms = _events_ms(bwd, 10, 3, flush)
     proj_ms = _events_ms(lambda: r.project(d), 10, 3, flush)
     bin_ms = _events_ms(lambda: r.bin_sort(), 10, 3, flush)
+    g3 = dict(dmeans3=torch.zeros_like(d["means3"]), dscales=torch.zeros_like(d["scales"]),
+              dquats=torch.zeros_like(d["quats"]), dsh=torch.zeros_like(d["sh"]))
+    pbwd_ms = _events_ms(lambda: tc.tcgs_project_bwd(r.cam, d["means3"], d["scales"], d["quats"], d["sh"],
+                                                     d["sh_degree"], r.proj["radius"], grads["dmean2d"],
+                                                     grads["dconic"], grads["drgb"], grads=g3), 10, 3, flush)
     return {"workload": "differentiation: 1280x720, fx=fy=1280, 500k Gaussians (plain distributions), L1 to a "
                         "seeded target; backward replays the FP32 forward", "splats": n,
             "alpha_evals": st[0] + st[1], "f_blend": st[0],
             "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
-                   "render_fwd_tc": fwdtc, "render_bwd": bwd_ms},
-            "train_step_ms_fp32": proj_ms + bin_ms + fwd32 + bwd_ms,
-            "train_step_ms_tc_fwd": proj_ms + bin_ms + fwdtc + bwd_ms,
+                   "render_fwd_tc": fwdtc, "render_bwd": bwd_ms, "project_bwd": pbwd_ms},
+            "train_step_ms_fp32": proj_ms + bin_ms + fwd32 + bwd_ms + pbwd_ms,
+            "train_step_ms_tc_fwd": proj_ms + bin_ms + fwdtc + bwd_ms + pbwd_ms,
+            "train_step_note": "forward and backward to the 3D parameters (means, scales, quaternions, opacity, "
+                               "SH); per-stage CUDA events with L2 flushed before each stage",
             "bwd_alpha_evals_per_s": (st[0] + st[1]) / (bwd_ms * 1e-3)}
 
 

@@ -136,6 +136,26 @@ TCGS_API tcgs_status tcgs_project(const tcgs_camera* cam /* host */, int32_t P, 
                          const float* opacity /* nullable */, float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
                          uint32_t* tiles_touched, tcgs_stream stream);
 
+/*
+ * Backward of tcgs_project (Sec. 3.1, Eq. 2): given dL/d(mean2d, conic, rgb) of every Gaussian,
+ * accumulates (+=) dL/d(means3, scales, quats, sh).  conic is (sigma11, sigma12, sigma22) and
+ * dconic[1] is the derivative with respect to the one parameter sigma12 that fills both
+ * off-diagonal entries, as tcgs_render_bwd produces it.  Per Gaussian the forward is recomputed
+ * and differentiated step by step: conic = Sigma'^-1, Sigma' = J W Sigma W^T J^T + 0.3 I (J at the
+ * frustum-clamped mean: a clamped coordinate passes no gradient through J), Sigma = M M^T with
+ * M = R(q / |q|) diag(s), mean2d of the camera-space mean, and the SH colour including its
+ * view-direction term (a colour channel clamped at 0 passes none).  Depth, radius and the
+ * culling decisions are not differentiable; Gaussians with radius[g] <= 0 are skipped.
+ * In:  as tcgs_project (without opacity), radius [P] int32 from the forward, dmean2d [P,2],
+ *      dconic [P,3], drgb [P,3].
+ * Out: dmeans3 [P,3], dscales [P,3], dquats [P,4], dsh [P, (sh_degree+1)^2, 3], accumulated.
+ */
+TCGS_API tcgs_status tcgs_project_bwd(const tcgs_camera* cam /* host */, int32_t P, int32_t sh_degree,
+                             const float* means3, const float* scales, const float* quats, const float* sh,
+                             const int32_t* radius, const float* dmean2d, const float* dconic,
+                             const float* drgb, float* dmeans3, float* dscales, float* dquats, float* dsh,
+                             tcgs_stream stream);
+
 /* Bytes of device workspace tcgs_bin_sort needs (a pure host function). */
 TCGS_API size_t tcgs_bin_sort_workspace_size(int32_t P, int64_t splat_capacity, int32_t num_tiles);
 

@@ -78,6 +78,8 @@ def _L():
                                                   P(d), P(d), P(d), P(i32)]
             lib.orc_render_bwd.argtypes = [cam, d, P(i32), P(i32), P(d), P(d), P(d), P(d), P(d), P(d),
                                            P(d), P(d), P(d), P(d)]
+            lib.orc_project_bwd.argtypes = [cam, ctypes.c_int, ctypes.c_int, P(d), P(d), P(d), P(d), P(i32),
+                                            P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
             _lib = lib
     return _lib
 
@@ -195,4 +197,21 @@ def render_bwd(cam: dict, binned: dict, mean2d, conic, opacity, rgb, dL_dimg, bg
                         _p(_i32(binned["ids"]), ctypes.c_int32), _p(_f64(mean2d), d), _p(_f64(conic), d),
                         _p(_f64(opacity), d), _p(_f64(rgb), d), _p(_f64(bg), d), _p(_f64(dL_dimg), d),
                         _p(out["dmean2d"], d), _p(out["dconic"], d), _p(out["dopacity"], d), _p(out["drgb"], d))
+    return out
+
+
+def project_bwd(cam: dict, scene: dict, radius, dmean2d, dconic, drgb) -> dict:
+    """Analytic gradient of the preprocess (Sec. 3.1, Eq. 2) w.r.t. means3, scales, quats and sh,
+    given the gradients of mean2d, conic and rgb; Gaussians with radius 0 get zeros."""
+    c = camera(cam)
+    means3 = _f64(scene["means3"]); P = means3.shape[0]
+    deg = int(scene["sh_degree"])
+    K = (deg + 1) ** 2
+    out = dict(dmeans3=np.zeros((P, 3)), dscales=np.zeros((P, 3)), dquats=np.zeros((P, 4)),
+               dsh=np.zeros((P, K, 3)))
+    d = ctypes.c_double
+    _L().orc_project_bwd(ctypes.byref(c), P, deg, _p(means3, d), _p(_f64(scene["scales"]), d),
+                         _p(_f64(scene["quats"]), d), _p(_f64(scene["sh"]), d), _p(_i32(radius), ctypes.c_int32),
+                         _p(_f64(dmean2d), d), _p(_f64(dconic), d), _p(_f64(drgb), d), _p(out["dmeans3"], d),
+                         _p(out["dscales"], d), _p(out["dquats"], d), _p(out["dsh"], d))
     return out

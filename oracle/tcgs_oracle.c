@@ -506,3 +506,211 @@ void orc_render_bwd(const orc_camera* cam, double alpha_max, const int32_t* rang
     }
     free(bj); free(ba); free(bT); free(bclamped);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Backward of the preprocess (Sec. 3.1, Eq. 2): given dL/d(mean2d, conic,   */
+/* rgb) of each Gaussian, dL/d(means3, scales, quats, sh), written.  The      */
+/* forward is recomputed step by step and every step is differentiated in    */
+/* reverse: conic = Sigma'^-1, Sigma' = T Sigma T^T + 0.3 I, T = J W,         */
+/* Sigma = M M^T, M = R(q/|q|) diag(s), J from the frustum-clamped mean,      */
+/* mean2d = (fx tx / tz + cx, fy ty / tz + cy), t = W mu + t0, and           */
+/* rgb = max(0, sum_k Y_k(dir) sh_k + 1/2), dir = (mu - campos) / |.|.       */
+/* conic holds (s11, s12, s22); dconic[1] is the derivative with respect to  */
+/* the one parameter s12 that fills both off-diagonal entries.  Gaussians    */
+/* with radius 0 (culled) get zero gradients.                                 */
+/* ------------------------------------------------------------------------ */
+
+/* d Y_k / d(x, y, z) of the basis of orc_sh_basis at a unit direction. */
+static void sh_basis_grad(int degree, const double dir[3], double dY[16][3])
+{
+    const double pi = 3.14159265358979323846;
+    double x = dir[0], y = dir[1], z = dir[2];
+    for (int k = 0; k < 16; ++k) dY[k][0] = dY[k][1] = dY[k][2] = 0.0;
+    if (degree < 1) return;
+    double k1 = sqrt(3.0 / (4.0 * pi));
+    dY[1][1] = -k1;
+    dY[2][2] = k1;
+    dY[3][0] = -k1;
+    if (degree < 2) return;
+    double k2a = 0.5 * sqrt(15.0 / pi), k20 = 0.25 * sqrt(5.0 / pi), k22 = 0.25 * sqrt(15.0 / pi);
+    dY[4][0] = k2a * y;          dY[4][1] = k2a * x;
+    dY[5][1] = -k2a * z;         dY[5][2] = -k2a * y;
+    dY[6][0] = -2.0 * k20 * x;   dY[6][1] = -2.0 * k20 * y;   dY[6][2] = 4.0 * k20 * z;
+    dY[7][0] = -k2a * z;         dY[7][2] = -k2a * x;
+    dY[8][0] = 2.0 * k22 * x;    dY[8][1] = -2.0 * k22 * y;
+    if (degree < 3) return;
+    double k33 = 0.25 * sqrt(35.0 / (2.0 * pi)), k32 = 0.5 * sqrt(105.0 / pi);
+    double k31 = 0.25 * sqrt(21.0 / (2.0 * pi)), k30 = 0.25 * sqrt(7.0 / pi), k32b = 0.25 * sqrt(105.0 / pi);
+    /* Y9 = -k33 (3 x^2 y - y^3) */
+    dY[9][0] = -6.0 * k33 * x * y;           dY[9][1] = -k33 * (3.0 * x * x - 3.0 * y * y);
+    /* Y10 = k32 x y z */
+    dY[10][0] = k32 * y * z;                 dY[10][1] = k32 * x * z;   dY[10][2] = k32 * x * y;
+    /* Y11 = -k31 (4 y z^2 - x^2 y - y^3) */
+    dY[11][0] = 2.0 * k31 * x * y;           dY[11][1] = -k31 * (4.0 * z * z - x * x - 3.0 * y * y);
+    dY[11][2] = -8.0 * k31 * y * z;
+    /* Y12 = k30 (2 z^3 - 3 x^2 z - 3 y^2 z) */
+    dY[12][0] = -6.0 * k30 * x * z;          dY[12][1] = -6.0 * k30 * y * z;
+    dY[12][2] = k30 * (6.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    /* Y13 = -k31 (4 x z^2 - x^3 - x y^2) */
+    dY[13][0] = -k31 * (4.0 * z * z - 3.0 * x * x - y * y);   dY[13][1] = 2.0 * k31 * x * y;
+    dY[13][2] = -8.0 * k31 * x * z;
+    /* Y14 = k32b (x^2 z - y^2 z) */
+    dY[14][0] = 2.0 * k32b * x * z;          dY[14][1] = -2.0 * k32b * y * z;   dY[14][2] = k32b * (x * x - y * y);
+    /* Y15 = -k33 (x^3 - 3 x y^2) */
+    dY[15][0] = -k33 * (3.0 * x * x - 3.0 * y * y);   dY[15][1] = 6.0 * k33 * x * y;
+}
+
+void orc_project_bwd(const orc_camera* cam, int P, int sh_degree,
+                     const double* means3, const double* scales, const double* quats, const double* sh,
+                     const int32_t* radius, const double* dmean2d, const double* dconic, const double* drgb,
+                     double* dmeans3, double* dscales, double* dquats, double* dsh)
+{
+    const double* V = cam->viewmat;
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    for (int g = 0; g < P; ++g) {
+        for (int i = 0; i < 3; ++i) dmeans3[3 * g + i] = dscales[3 * g + i] = 0.0;
+        for (int i = 0; i < 4; ++i) dquats[4 * g + i] = 0.0;
+        for (int i = 0; i < K * 3; ++i) dsh[(size_t)g * K * 3 + i] = 0.0;
+        if (radius[g] <= 0) continue;
+        const double* m = means3 + 3 * g;
+        const double* s = scales + 3 * g;
+        const double* q = quats + 4 * g;
+
+        /* ---- forward recomputation */
+        double t[3];
+        for (int i = 0; i < 3; ++i)
+            t[i] = V[4 * i] * m[0] + V[4 * i + 1] * m[1] + V[4 * i + 2] * m[2] + V[4 * i + 3];
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        double R[9];
+        orc_quat_to_rot(q, R);
+        double M[9], S3[9];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) M[3 * i + k] = R[3 * i + k] * s[k];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double a = 0.0;
+                for (int l = 0; l < 3; ++l) a += M[3 * i + l] * M[3 * k + l];
+                S3[3 * i + k] = a;
+            }
+        double limx = 1.3 * cam->tan_fovx, limy = 1.3 * cam->tan_fovy;
+        double u = t[0] / t[2], v = t[1] / t[2];
+        double cu = fmin(limx, fmax(-limx, u)), cv = fmin(limy, fmax(-limy, v));
+        double du = (u > -limx && u < limx) ? 1.0 : 0.0, dv = (v > -limy && v < limy) ? 1.0 : 0.0;
+        double tz = t[2];
+        double J[6] = {cam->fx / tz, 0.0, -cam->fx * cu / tz, 0.0, cam->fy / tz, -cam->fy * cv / tz};
+        double T[6];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 3; ++k)
+                T[3 * i + k] = J[3 * i] * V[k] + J[3 * i + 1] * V[4 + k] + J[3 * i + 2] * V[8 + k];
+        double C2[4];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 2; ++k) {
+                double a = 0.0;
+                for (int aa = 0; aa < 3; ++aa)
+                    for (int bb = 0; bb < 3; ++bb) a += T[3 * i + aa] * S3[3 * aa + bb] * T[3 * k + bb];
+                C2[2 * i + k] = a;
+            }
+        double A = C2[0] + 0.3, B = C2[1], C = C2[3] + 0.3;
+        double det = A * C - B * B;
+        double Q[4] = {C / det, -B / det, -B / det, A / det};
+
+        /* ---- conic -> Sigma':  dL/dSigma' = -Q G Q, G the symmetric matrix of dconic */
+        const double* dc = dconic + 3 * g;
+        double G[4] = {dc[0], 0.5 * dc[1], 0.5 * dc[1], dc[2]};
+        double QG[4], H[4];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 2; ++k) QG[2 * i + k] = Q[2 * i] * G[k] + Q[2 * i + 1] * G[2 + k];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 2; ++k) H[2 * i + k] = -(QG[2 * i] * Q[k] + QG[2 * i + 1] * Q[2 + k]);
+
+        /* ---- Sigma' = T Sigma T^T:  dL/dT = 2 H T Sigma, dL/dSigma = T^T H T */
+        double TS[6], dT[6], dS[9];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double a = 0.0;
+                for (int l = 0; l < 3; ++l) a += T[3 * i + l] * S3[3 * l + k];
+                TS[3 * i + k] = a;
+            }
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 3; ++k) dT[3 * i + k] = 2.0 * (H[2 * i] * TS[k] + H[2 * i + 1] * TS[3 + k]);
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double a = 0.0;
+                for (int aa = 0; aa < 2; ++aa)
+                    for (int bb = 0; bb < 2; ++bb) a += T[3 * aa + i] * H[2 * aa + bb] * T[3 * bb + k];
+                dS[3 * i + k] = a;
+            }
+
+        /* ---- T = J W:  dL/dJ = dL/dT W^T (W the rotation part of the view matrix) */
+        double dJ[6];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 3; ++k)
+                dJ[3 * i + k] = dT[3 * i] * V[4 * k] + dT[3 * i + 1] * V[4 * k + 1] + dT[3 * i + 2] * V[4 * k + 2];
+
+        /* ---- J(t) and mean2d(t) -> dL/dt */
+        const double* dm2 = dmean2d + 2 * g;
+        double dt[3];
+        dt[0] = cam->fx / tz * dm2[0] + dJ[2] * (-cam->fx * du / (tz * tz));
+        dt[1] = cam->fy / tz * dm2[1] + dJ[5] * (-cam->fy * dv / (tz * tz));
+        dt[2] = -cam->fx * t[0] / (tz * tz) * dm2[0] - cam->fy * t[1] / (tz * tz) * dm2[1]
+                + dJ[0] * (-cam->fx / (tz * tz)) + dJ[4] * (-cam->fy / (tz * tz))
+                + dJ[2] * cam->fx * (du * t[0] / (tz * tz * tz) + cu / (tz * tz))
+                + dJ[5] * cam->fy * (dv * t[1] / (tz * tz * tz) + cv / (tz * tz));
+        double* dmu = dmeans3 + 3 * g;
+        for (int k = 0; k < 3; ++k) dmu[k] = V[k] * dt[0] + V[4 + k] * dt[1] + V[8 + k] * dt[2];
+
+        /* ---- Sigma = M M^T:  dL/dM = 2 dS M;  M = R diag(s) */
+        double dM[9];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double a = 0.0;
+                for (int l = 0; l < 3; ++l) a += (dS[3 * i + l] + dS[3 * l + i]) * M[3 * l + k];
+                dM[3 * i + k] = a;
+            }
+        double dR[9];
+        for (int k = 0; k < 3; ++k) {
+            double a = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                a += dM[3 * i + k] * R[3 * i + k];
+                dR[3 * i + k] = dM[3 * i + k] * s[k];
+            }
+            dscales[3 * g + k] = a;
+        }
+        /* ---- R(w, x, y, z) of the unit quaternion, then the normalisation q / |q| */
+        double dqn[4];
+        dqn[0] = dR[1] * (-2 * z) + dR[2] * (2 * y) + dR[3] * (2 * z) + dR[5] * (-2 * x) + dR[6] * (-2 * y)
+                 + dR[7] * (2 * x);
+        dqn[1] = dR[1] * (2 * y) + dR[2] * (2 * z) + dR[3] * (2 * y) + dR[4] * (-4 * x) + dR[5] * (-2 * w)
+                 + dR[6] * (2 * z) + dR[7] * (2 * w) + dR[8] * (-4 * x);
+        dqn[2] = dR[0] * (-4 * y) + dR[1] * (2 * x) + dR[2] * (2 * w) + dR[3] * (2 * x) + dR[5] * (2 * z)
+                 + dR[6] * (-2 * w) + dR[7] * (2 * z) + dR[8] * (-4 * y);
+        dqn[3] = dR[0] * (-4 * z) + dR[1] * (-2 * w) + dR[2] * (2 * x) + dR[3] * (2 * w) + dR[4] * (-4 * z)
+                 + dR[5] * (2 * y) + dR[6] * (2 * x) + dR[7] * (2 * y);
+        double qh[4] = {w, x, y, z};
+        double dot = qh[0] * dqn[0] + qh[1] * dqn[1] + qh[2] * dqn[2] + qh[3] * dqn[3];
+        for (int i = 0; i < 4; ++i) dquats[4 * g + i] = (dqn[i] - qh[i] * dot) / qn;
+
+        /* ---- colour: rgb = max(0, sum_k Y_k(dir) sh_k + 1/2) */
+        double d[3] = {m[0] - cam->campos[0], m[1] - cam->campos[1], m[2] - cam->campos[2]};
+        double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double dir[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+        double Y[16], dY[16][3];
+        orc_sh_basis(sh_degree, dir, Y);
+        sh_basis_grad(sh_degree, dir, dY);
+        const double* shg = sh + (size_t)g * K * 3;
+        double* dshg = dsh + (size_t)g * K * 3;
+        double ddir[3] = {0.0, 0.0, 0.0};
+        for (int ch = 0; ch < 3; ++ch) {
+            double a = 0.5;
+            for (int k = 0; k < K; ++k) a += Y[k] * shg[3 * k + ch];
+            double gc = a < 0.0 ? 0.0 : drgb[3 * g + ch];
+            for (int k = 0; k < K; ++k) {
+                dshg[3 * k + ch] = Y[k] * gc;
+                for (int j = 0; j < 3; ++j) ddir[j] += gc * shg[3 * k + ch] * dY[k][j];
+            }
+        }
+        double dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+        for (int j = 0; j < 3; ++j) dmu[j] += (ddir[j] - dir[j] * dd) / dn;
+    }
+}

@@ -24,9 +24,9 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_GLOBAL, TCG
 
 TILE = 16
 
-__all__ = ["tcgs_project", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
+__all__ = ["tcgs_project", "tcgs_project_bwd", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
-           "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "TcgsError", "PRECISIONS",
+           "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
            "TCGS_TC_TF32_GLOBAL"]
 
@@ -108,6 +108,24 @@ def tcgs_project(cam, means3, scales, quats, sh, sh_degree, out=None, stream=Non
         _ptr(out["depth"], f), _ptr(out["radius"], torch.int32), _ptr(out["rgb"], f),
         _ptr(out["tiles_touched"], torch.int32), _stream(stream)))
     return out
+
+
+def tcgs_project_bwd(cam, means3, scales, quats, sh, sh_degree, radius, dmean2d, dconic, drgb, grads=None,
+                     stream=None) -> dict:
+    """Accumulates dL/d(means3, scales, quats, sh) into ``grads`` (zeros when None) and returns it."""
+    c = _cam(cam)
+    P = means3.shape[0]
+    if grads is None:
+        grads = dict(dmeans3=torch.zeros_like(means3), dscales=torch.zeros_like(scales),
+                     dquats=torch.zeros_like(quats), dsh=torch.zeros_like(sh))
+    f = torch.float32
+    check("tcgs_project_bwd", _L().tcgs_project_bwd(
+        ctypes.byref(c), P, int(sh_degree), _ptr(means3, f, "means3"), _ptr(scales, f, "scales"),
+        _ptr(quats, f, "quats"), _ptr(sh, f, "sh"), _ptr(radius, torch.int32, "radius"),
+        _ptr(dmean2d, f, "dmean2d"), _ptr(dconic, f, "dconic"), _ptr(drgb, f, "drgb"),
+        _ptr(grads["dmeans3"], f), _ptr(grads["dscales"], f), _ptr(grads["dquats"], f), _ptr(grads["dsh"], f),
+        _stream(stream)))
+    return grads
 
 
 def tcgs_bin_sort_workspace_size(P: int, capacity: int, num_tiles: int) -> int:
@@ -390,3 +408,40 @@ def rasterize(mean2d, conic, opacity, rgb, cam, tile_ranges, ids_sorted, precisi
     to mean2d, conic, opacity and rgb through the library's backward kernel."""
     return _Rasterize.apply(mean2d, conic, opacity, rgb, _cam(cam), tile_ranges, ids_sorted, precision, alpha_max,
                             tuple(bg))
+
+
+class _Project(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means3, scales, quats, sh, cam, sh_degree, radius_opacity):
+        out = tcgs_project(cam, means3, scales, quats, sh, sh_degree, opacity=radius_opacity)
+        ctx.cam, ctx.sh_degree = cam, sh_degree
+        ctx.save_for_backward(means3, scales, quats, sh, out["radius"])
+        ctx.mark_non_differentiable(out["depth"], out["radius"], out["tiles_touched"])
+        return out["mean2d"], out["conic"], out["rgb"], out["depth"], out["radius"], out["tiles_touched"]
+
+    @staticmethod
+    def backward(ctx, g_mean2d, g_conic, g_rgb, g_depth, g_radius, g_tiles):
+        means3, scales, quats, sh, radius = ctx.saved_tensors
+        zeros = lambda t, g: g.contiguous() if g is not None else torch.zeros_like(t)
+        P = means3.shape[0]
+        dev = means3.device
+        g = tcgs_project_bwd(ctx.cam, means3, scales, quats, sh, ctx.sh_degree, radius,
+                             zeros(torch.empty(P, 2, device=dev), g_mean2d), zeros(torch.empty(P, 3, device=dev), g_conic),
+                             zeros(torch.empty(P, 3, device=dev), g_rgb))
+        return g["dmeans3"], g["dscales"], g["dquats"], g["dsh"], None, None, None
+
+
+def render_gaussians(cam, means3, scales, quats, opacity, sh, sh_degree, precision="tc_fp16_split", alpha_max=0.99,
+                     bg=(0.0, 0.0, 0.0), tight_radius=False, capacity=None):
+    """Differentiable frame from 3D Gaussians: project -> bin_sort -> render.  Gradients flow to
+    means3, scales, quats, opacity and sh through tcgs_render_bwd and tcgs_project_bwd (binning is
+    piecewise constant).  Returns (img [3,H,W], T_final [H,W]).  capacity None sizes the splat
+    buffer from the projection (one host synchronisation)."""
+    c = _cam(cam)
+    mean2d, conic, rgb, depth, radius, tiles = _Project.apply(means3, scales, quats, sh, c, int(sh_degree),
+                                                              opacity.detach() if tight_radius else None)
+    if capacity is None:
+        capacity = int(tiles.to(torch.int64).sum().item()) + 1
+    bins = tcgs_bin_sort(c, mean2d.detach(), radius, depth, capacity)
+    return rasterize(mean2d, conic, opacity, rgb, c, bins["tile_ranges"], bins["ids_sorted"], precision, alpha_max,
+                     bg)

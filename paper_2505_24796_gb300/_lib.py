@@ -54,6 +54,7 @@ SIGNATURES = {
     "tcgs_version": (ctypes.c_int, []),
     "tcgs_kernel_launches": (ctypes.c_uint64, []),
     "tcgs_project": (c_int32, [P_CAM, c_int32, c_int32, V, V, V, V, V, V, V, V, V, V, V, V]),
+    "tcgs_project_bwd": (c_int32, [P_CAM, c_int32, c_int32] + [V] * 12 + [V]),
     "tcgs_bin_sort_workspace_size": (c_size_t, [c_int32, c_int64, c_int32]),
     "tcgs_bin_sort": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
     "tcgs_bin_sort_noalloc": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, V, V, V, V]),

@@ -424,3 +424,64 @@ def test_tc_block_culling_changes_nothing(tc, name, make, precision):
         # skipping only removes entries that are culled in exact arithmetic: never further from the oracle
         assert psnr(res[True][0]["img"], o["img"]) >= psnr(res[False][0]["img"], o["img"]) - 0.05
     assert res[True][1][:, 2].sum() < res[False][1][:, 2].sum()
+
+
+# ------------------------------------------------------------------ projection backward
+
+def _rel_err_per_gaussian(got, ref):
+    got = got.reshape(len(got), -1).astype(np.float64)
+    ref = ref.reshape(len(ref), -1)
+    scale = np.abs(ref).max(axis=1) + 1e-6 * (np.abs(ref).max() + 1e-30)
+    return np.abs(got - ref).max(axis=1) / scale
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_project_backward_matches_oracle(tc, name, make):
+    cam, sc = make()
+    pr = oracle.project(cam, scene64(sc))
+    P = len(sc["opacity"])
+    rng = np.random.default_rng(31)
+    wm, wc, wr = f32(rng.normal(size=(P, 2))), f32(rng.normal(size=(P, 3))), f32(rng.normal(size=(P, 3)))
+    ref = oracle.project_bwd(cam, scene64(sc), pr["radius"], wm, wc, wr)
+    dsc = tc.scene_to_device(sc, DEV)
+    g = tc.tcgs_project_bwd(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], sc["sh_degree"],
+                            to_torch(pr["radius"].astype(np.int32), DEV), to_torch(wm, DEV), to_torch(wc, DEV),
+                            to_torch(wr, DEV))
+    torch.cuda.synchronize()
+    vis = pr["radius"] > 0
+    for key in ("dmeans3", "dscales", "dquats", "dsh"):
+        got = g[key].cpu().numpy()
+        assert (got[~vis] == 0).all()
+        e = _rel_err_per_gaussian(got[vis], ref[key][vis])
+        print(f"\n[project bwd] {name} {key}: median rel err {np.median(e):.2e}, 99.9% {np.quantile(e, 0.999):.2e}, "
+              f"max {e.max():.2e}")
+        assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 2e-3, (key, e.max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tc_fp16_split"])
+def test_render_gaussians_gradients_match_oracle_chain(tc, precision):
+    """End to end: autograd through the library's render and projection backward kernels against
+    the oracle's render backward followed by its projection backward."""
+    cam, sc = scenes.plain_forward(P=400, width=96, height=64, seed=21)
+    sc = dict(sc)
+    sc["scales"] = f32(sc["scales"] * 2.0)
+    s64 = scene64(sc)
+    rng = np.random.default_rng(22)
+    G = f32(rng.standard_normal((3, 64, 96)))
+    pr = oracle.project(cam, s64)
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    rb = oracle.render_bwd(cam, b, pr["mean2d"], pr["conic"], s64["opacity"], pr["rgb"], G)
+    ref = oracle.project_bwd(cam, s64, pr["radius"], rb["dmean2d"], rb["dconic"], rb["drgb"])
+    ref["dopacity"] = rb["dopacity"]
+    leaves = {k: to_torch(sc[k], DEV).requires_grad_(True) for k in ("means3", "scales", "quats", "opacity", "sh")}
+    img, _ = tc.render_gaussians(cam, leaves["means3"], leaves["scales"], leaves["quats"], leaves["opacity"],
+                                 leaves["sh"], sc["sh_degree"], precision=precision)
+    (img * to_torch(G, DEV)).sum().backward()
+    torch.cuda.synchronize()
+    vis = pr["radius"] > 0
+    for key, leaf in [("dmeans3", "means3"), ("dscales", "scales"), ("dquats", "quats"), ("dopacity", "opacity"),
+                      ("dsh", "sh")]:
+        got = leaves[leaf].grad.cpu().numpy()
+        e = _rel_err_per_gaussian(got[vis], ref[key][vis])
+        print(f"\n[end to end {precision}] {key}: median rel err {np.median(e):.2e}, 99% {np.quantile(e, 0.99):.2e}")
+        assert np.quantile(e, 0.99) <= 1e-3, (key, np.quantile(e, 0.99))

@@ -695,3 +695,108 @@ def test_backward_clamped_alpha_finite_differences():
             fd = ((op_["img"] * gimg).sum() - (om_["img"] * gimg).sum()) / (2 * h)
             an = grads[name].reshape(3, -1)[0, k]
             assert abs(fd - an) <= 2e-5 * max(1.0, abs(an)), (name, k, fd, an)
+
+
+# ---------------------------------------------------------------- projection backward
+
+def _project_fd_case(seed, deg=3, clamp=False):
+    rng = np.random.default_rng(seed)
+    P = 12
+    cam = scenes.pinhole(160, 120, fx=150.0)
+    R = Rotation.from_rotvec(rng.normal(0, 0.2, 3)).as_matrix()
+    cam["viewmat"] = np.hstack([R, rng.normal(0, 0.3, (3, 1))]).reshape(-1).tolist()
+    cam["campos"] = (-R.T @ np.asarray(cam["viewmat"]).reshape(3, 4)[:, 3]).tolist()
+    means3 = np.c_[rng.uniform(-1, 1, P), rng.uniform(-0.8, 0.8, P), rng.uniform(3, 6, P)]
+    means3 = (R.T @ (means3.T - np.asarray(cam["viewmat"]).reshape(3, 4)[:, 3:])).T   # in front of the camera
+    scales = np.exp(rng.normal(-2.5, 0.4, (P, 3)))
+    if clamp:   # far outside the frustum in x, large enough to still touch the image
+        t = np.asarray(cam["viewmat"]).reshape(3, 4)
+        cm = np.c_[np.full(P, 3.5), rng.uniform(-0.5, 0.5, P), np.full(P, 2.0)]
+        means3 = (R.T @ (cm.T - t[:, 3:])).T
+        scales = np.full((P, 3), 1.5)
+    sc = dict(means3=means3, scales=scales, quats=rng.normal(0, 1, (P, 4)) * 2.0, opacity=np.full(P, 0.5),
+              sh=rng.normal(0, 0.3, (P, (deg + 1) ** 2, 3)), sh_degree=deg)
+    sc["sh"][:, 0, :] = 1.0   # colours away from the clamp at 0
+    return cam, sc
+
+
+@pytest.mark.parametrize("seed,deg,clamp", [(40, 3, False), (41, 1, False), (42, 3, True)])
+def test_project_backward_matches_finite_differences(seed, deg, clamp):
+    cam, sc = _project_fd_case(seed, deg, clamp)
+    rng = np.random.default_rng(seed + 100)
+    pr = oracle.project(cam, sc)
+    vis = pr["radius"] > 0
+    assert vis.sum() >= 6
+    P = len(vis)
+    wm, wc, wr = rng.normal(size=(P, 2)), rng.normal(size=(P, 3)), rng.normal(size=(P, 3))
+    if clamp:
+        txtz = np.array([(np.asarray(cam["viewmat"]).reshape(3, 4) @ np.r_[m, 1.0]) for m in sc["means3"]])
+        assert (txtz[:, 0] / txtz[:, 2] > 1.3 * cam["width"] / (2 * cam["fx"]))[vis].all()   # clamped Jacobian
+
+    def loss(s):
+        o = oracle.project(cam, s)
+        return float((o["mean2d"] * wm).sum() + (o["conic"] * wc).sum() + (o["rgb"] * wr).sum())
+
+    g = oracle.project_bwd(cam, sc, pr["radius"], wm, wc, wr)
+    grads = dict(means3=g["dmeans3"], scales=g["dscales"], quats=g["dquats"], sh=g["dsh"])
+    for name, h in [("means3", 1e-6), ("scales", 1e-7), ("quats", 1e-6), ("sh", 1e-6)]:
+        base = sc[name]
+        for gid in np.nonzero(vis)[0][:6]:
+            for k in range(base[gid].size):
+                sp = {kk: (vv.copy() if isinstance(vv, np.ndarray) else vv) for kk, vv in sc.items()}
+                sm = {kk: (vv.copy() if isinstance(vv, np.ndarray) else vv) for kk, vv in sc.items()}
+                sp[name][gid].reshape(-1)[k] += h
+                sm[name][gid].reshape(-1)[k] -= h
+                fd = (loss(sp) - loss(sm)) / (2 * h)
+                an = grads[name][gid].reshape(-1)[k]
+                assert abs(fd - an) <= 2e-5 * max(1.0, abs(an)), (name, gid, k, fd, an)
+    # culled Gaussians get zero gradients
+    assert (g["dmeans3"][~vis] == 0).all()
+
+
+def test_end_to_end_gradient_chain_matches_finite_differences():
+    """dL/d(3D parameters) of L = sum(img * G) through Algorithm 1 and the preprocess: the
+    oracle's render backward followed by its projection backward (the conic convention of the
+    two must agree) against central differences of the whole oracle forward."""
+    cam, sc = scenes.plain_forward(P=120, width=48, height=48, seed=7)
+    sc = scene_arrays(sc)
+    sc["scales"] = sc["scales"] * 3.0
+    op = sc["opacity"]
+    rng = np.random.default_rng(8)
+    G = rng.standard_normal((3, 48, 48))
+    pr = oracle.project(cam, sc)
+    b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    ref = oracle.render(cam, b, pr["mean2d"], pr["conic"], op, pr["rgb"])
+    rb = oracle.render_bwd(cam, b, pr["mean2d"], pr["conic"], op, pr["rgb"], G)
+    g = oracle.project_bwd(cam, sc, pr["radius"], rb["dmean2d"], rb["dconic"], rb["drgb"])
+
+    def loss(s):
+        p2 = oracle.project(cam, s)
+        if not np.array_equal(p2["radius"], pr["radius"]):
+            return None, False
+        b2 = oracle.bin_sort(cam, p2["mean2d"], p2["radius"], p2["depth"])
+        o = oracle.render(cam, b2, p2["mean2d"], p2["conic"], op, p2["rgb"])
+        same = np.array_equal(b2["ids"], b["ids"]) and np.array_equal(o["n_eval"], ref["n_eval"]) and \
+            np.array_equal(o["n_contrib"], ref["n_contrib"])
+        return float((o["img"] * G).sum()), same
+
+    vis = np.nonzero(pr["radius"] > 0)[0]
+    cand = vis[np.argsort(-np.abs(rb["dopacity"][vis]))[:8]]
+    checked = 0
+    for name, h, key in [("means3", 1e-6, "dmeans3"), ("scales", 1e-7, "dscales"), ("quats", 1e-6, "dquats"),
+                         ("sh", 1e-6, "dsh")]:
+        for gid in cand[:5]:
+            for k in range(sc[name][gid].size):
+                sp = {kk: (vv.copy() if isinstance(vv, np.ndarray) else vv) for kk, vv in sc.items()}
+                sm = {kk: (vv.copy() if isinstance(vv, np.ndarray) else vv) for kk, vv in sc.items()}
+                sp[name][gid].reshape(-1)[k] += h
+                sm[name][gid].reshape(-1)[k] -= h
+                lp, s1 = loss(sp)
+                lm, s2 = loss(sm)
+                if not (s1 and s2):
+                    continue   # a discrete decision moved: not differentiable here
+                fd = (lp - lm) / (2 * h)
+                an = g[key][gid].reshape(-1)[k]
+                assert abs(fd - an) <= 1e-4 * max(1.0, abs(an)), (name, gid, k, fd, an)
+                checked += 1
+    assert checked >= 60
