@@ -77,7 +77,7 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* warp_sums, T& total) {
 
 template <int KI>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
-                                                         const uint32_t* n_dev, int shift, int G,
+                                                         const uint32_t* n_dev, int shift, uint32_t mask, int G,
                                                          uint32_t* __restrict__ hist,
                                                          uint32_t* __restrict__ digit_total) {
     __shared__ uint32_t h[kWarps][kRadix];
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
     __syncthreads();
     uint32_t lo, hi;
     block_range<kThreads * KI>(load_n(n_host, n_dev), G, lo, hi);
-    for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & 0xFFu], 1u);
+    for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
     __syncthreads();
     uint32_t s = 0;
 #pragma unroll
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, uint32_t n_host,
-                                                            const uint32_t* n_dev, int shift, int G,
+                                                            const uint32_t* n_dev, int shift, uint32_t mask, int G,
                                                             const uint32_t* __restrict__ offsets) {
     constexpr int TI = kThreads * KI;
     __shared__ uint32_t wcnt[kWarps][kRadix];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
 #pragma unroll
         for (int r = 0; r < KI; ++r) {
             const bool valid = base + r * 32 + lane < hi;
-            const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u | lane);
+            const uint32_t d = valid ? ((k[r] >> shift) & mask) : (0x100u | lane);
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             uint32_t before = 0;
             if (valid) before = wcnt[warp][d];
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
             const uint32_t i = (uint32_t)t + (uint32_t)q * kThreads;
             if (i < tile_n) {
                 const uint32_t key = sk[i];
-                const uint32_t d = (key >> shift) & 0xFFu;
+                const uint32_t d = (key >> shift) & mask;
                 const uint32_t gp = boff[d] + (i - tstart[d]);
                 keys_out[gp] = key;
                 vals_out[gp] = sv[i];
@@ -448,18 +448,20 @@ inline int sort_blocks(int64_t n) {
     return (int)(tiles < wave ? tiles : wave);
 }
 
-// One LSD pass; digit totals ping-pong between two 256-word buffers (the scan of a pass zeroes
-// the buffer the next pass accumulates into).
+// One LSD pass on the digit of `bits` (<= 8) bits at `shift`; digit totals ping-pong between two
+// 256-word buffers (the scan of a pass zeroes the buffer the next pass accumulates into).
 template <int KI>
 inline void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n_host,
-                       const uint32_t* n_dev, int shift, int G, const Workspace& w, int pass, cudaStream_t s) {
+                       const uint32_t* n_dev, int shift, int bits, int G, const Workspace& w, int pass,
+                       cudaStream_t s) {
     uint32_t* tot = w.digit_total + (pass & 1) * kRadix;
     uint32_t* nxt = w.digit_total + ((pass + 1) & 1) * kRadix;
-    k_radix_hist<KI><<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, G, w.hist, tot);
+    const uint32_t mask = (1u << bits) - 1u;
+    k_radix_hist<KI><<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, mask, G, w.hist, tot);
     count_launches(1);
     k_radix_scan<<<kRadix, kThreads, 0, s>>>(w.hist, tot, nxt, G);
     count_launches(1);
-    k_radix_scatter<KI><<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, G, w.hist);
+    k_radix_scatter<KI><<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, mask, G, w.hist);
     count_launches(1);
 }
 
@@ -505,7 +507,7 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
         for (int sh = 0; sh < 32; sh += 8, ++pass) {
             bool even = (pass & 1) == 0;
             radix_pass<kItems>(even ? w.dk_a : w.dk_b, even ? w.dv_a : w.dv_b, even ? w.dk_b : w.dk_a,
-                       even ? w.dv_b : w.dv_a, (uint32_t)P, nullptr, sh, Gp, w, pass, s);
+                       even ? w.dv_b : w.dv_a, (uint32_t)P, nullptr, sh, 8, Gp, w, pass, s);
         }
         TCGS_CHECK_LAUNCH();
     }
@@ -534,10 +536,13 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
                                                                   mean2d, radius, kbuf[src], vbuf[src], w.n_u32);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
-    // 4. stable sort by tile id
+    // 4. stable sort by tile id, 8 bits per pass (an even split of the tile bits measured slower)
     int Gs = sort_blocks<kItemsSplat>(splat_capacity);
-    for (int tp = 0; tp < tpasses; ++tp, ++pass) {
-        radix_pass<kItemsSplat>(kbuf[src], vbuf[src], kbuf[src ^ 1], vbuf[src ^ 1], 0u, w.n_u32, 8 * tp, Gs, w, pass, s);
+    for (int tp = 0, shift = 0; tp < tpasses; ++tp, ++pass) {
+        const int bits = tile_bits - shift < 8 ? tile_bits - shift : 8;
+        radix_pass<kItemsSplat>(kbuf[src], vbuf[src], kbuf[src ^ 1], vbuf[src ^ 1], 0u, w.n_u32, shift, bits, Gs, w,
+                                pass, s);
+        shift += bits;
         src ^= 1;
     }
     TCGS_CHECK_LAUNCH();
@@ -607,10 +612,10 @@ extern "C" tcgs_status tcgs_sched_order(const float* cost, const uint32_t* items
     w.digit_total = o.digit_total;
     const int G = sort_blocks<kItems>(n);
     // 0 -> 1 -> 0 -> 1 -> out
-    radix_pass<kItems>(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 0, G, w, 0, s);
-    radix_pass<kItems>(o.k1, o.v1, o.k0, o.v0, (uint32_t)n, nullptr, 8, G, w, 1, s);
-    radix_pass<kItems>(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 16, G, w, 2, s);
-    radix_pass<kItems>(o.k1, o.v1, o.k0, queue_out, (uint32_t)n, nullptr, 24, G, w, 3, s);
+    radix_pass<kItems>(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 0, 8, G, w, 0, s);
+    radix_pass<kItems>(o.k1, o.v1, o.k0, o.v0, (uint32_t)n, nullptr, 8, 8, G, w, 1, s);
+    radix_pass<kItems>(o.k0, o.v0, o.k1, o.v1, (uint32_t)n, nullptr, 16, 8, G, w, 2, s);
+    radix_pass<kItems>(o.k1, o.v1, o.k0, queue_out, (uint32_t)n, nullptr, 24, 8, G, w, 3, s);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
 }
