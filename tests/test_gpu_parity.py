@@ -163,6 +163,33 @@ def test_bin_sort_depth_ties_and_huge_gaussian(tc):
     np.testing.assert_array_equal(out["tile_ranges"].cpu().numpy(), b["ranges"])
 
 
+@pytest.mark.parametrize("depths", ["distinct", "short_ties", "three_levels", "all_equal"])
+def test_bin_sort_long_lists(tc, depths):
+    """Tiles with lists far longer than the shared-memory sort (thousands of splats per tile), so
+    each tile's depth sort runs in chunked passes through global memory; depth ties from none to
+    every splat of a tile being equal."""
+    cam = scenes.pinhole(100, 70, fx=100.0)
+    rng = np.random.default_rng(17)
+    P = 20_000
+    mean2d = f32(np.c_[rng.uniform(-10, 110, P), rng.uniform(-10, 80, P)])
+    radius = rng.integers(0, 48, P).astype(np.int32)
+    depth = f32(rng.uniform(0.5, 40.0, P))
+    if depths == "short_ties":
+        depth[::5] = depth[1::5]
+    elif depths == "three_levels":
+        depth = f32(rng.choice([1.0, 2.0, 3.0], P))
+    elif depths == "all_equal":
+        depth = np.full(P, 4.0, np.float32)
+    b = oracle.bin_sort(cam, mean2d, radius, depth)
+    lens = np.diff(b["ranges"], axis=1).ravel()
+    assert lens.min() > 2048 and lens.max() > 3 * 2048
+    out = tc.tcgs_bin_sort(cam, to_torch(mean2d, DEV), to_torch(radius, DEV), to_torch(depth, DEV), capacity=b["n"])
+    torch.cuda.synchronize()
+    assert int(out["status"].item()) == 0 and int(out["n_splats"].item()) == b["n"]
+    np.testing.assert_array_equal(out["ids_sorted"].cpu().numpy()[: b["n"]], b["ids"])
+    np.testing.assert_array_equal(out["tile_ranges"].cpu().numpy(), b["ranges"])
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
