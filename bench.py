@@ -313,6 +313,10 @@ def bench_scheduler(dev, train_views=200, chunk=16):
         sim[policy] = osc.lpt_makespan([cyc[i] for i in q.cpu().numpy().tolist()], workers)
     res["batched_render_ms"] = times
     res["simulated_makespan_cycles"] = sim
+    cyc_all = np.asarray(list(cyc.values()), dtype=np.float64)
+    # no order of whole tiles can finish before the heaviest tile, nor before the work spread evenly
+    res["makespan_lower_bound_cycles"] = {"heaviest_tile": float(cyc_all.max()),
+                                          "even_spread": float(cyc_all.sum() / workers)}
     res["gain_vs_length"] = times["length"] / times["mlp"]
     res["gain_vs_natural"] = times["natural"] / times["mlp"]
     return res
