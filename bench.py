@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the differentiation, scheduler and large workloads (reported beside the headline)")
     ap.add_argument("--sched-train-views", type=int, default=200)
+    ap.add_argument("--coverage", default="square", choices=["square", "exact"],
+                    help="tile coverage of the headline binning: the 3-sigma square of the paper's pipeline, or "
+                         "exact (tcgs_bin_sort_exact); the other one is timed beside it")
     return ap.parse_args()
 
 
@@ -230,6 +233,7 @@ def bench_differentiation(dev, flush):
     torch.cuda.synchronize()
     st = r.stats.to(torch.int64).sum(0).tolist()
     r.stats = None
+    exact = _exact_coverage_render(cam, d, n + 1024, dev, flush)
     tgt = torch.from_numpy(target).to(dev)
     gimg = torch.sign(r.out["img"] - tgt).contiguous()
     P = len(sc["opacity"])
@@ -254,6 +258,7 @@ def bench_differentiation(dev, flush):
                                                      grads["dconic"], grads["drgb"], grads=g3), 10, 3, flush)
     return {"workload": "differentiation: 1280x720, fx=fy=1280, 500k Gaussians (plain distributions), L1 to a "
                         "seeded target; backward replays the FP32 forward", "splats": n,
+            "exact_coverage": exact,
             "alpha_evals": st[0] + st[1], "f_blend": st[0],
             "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
                    "render_fwd_tc": fwdtc, "render_bwd": bwd_ms, "project_bwd": pbwd_ms},
@@ -356,6 +361,23 @@ def bench_large(dev, flush, steps=5, warmup=2):
     out["render_bwd_ms"] = _events_ms(lambda: tc.tcgs_render_bwd(
         r.cam, opts, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"], r.proj["conic"], d["opacity"],
         r.proj["rgb"], r.out["img"], r.out["T_final"], r.out["n_contrib"], gimg, grads=grads), 3, 1, flush)
+    del r
+    torch.cuda.empty_cache()
+    out["exact_coverage"] = _exact_coverage_render(cam, d, n + 1024, dev, flush, steps, warmup)
+    return out
+
+
+def _exact_coverage_render(cam, d, capacity, dev, flush, steps=10, warmup=3):
+    """The same view binned with exact tile coverage: splats, bin_sort and both renderers' times."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    r = tc.Renderer(cam, d["means3"].shape[0], capacity, device=dev, exact_tiles=True)
+    r.frame(d, precision="fp32")
+    torch.cuda.synchronize()
+    out = {"splats": int(r.bins["n_splats"].item()),
+           "ms": {"bin_sort": _events_ms(lambda: r.bin_sort(), steps, warmup, flush),
+                  "render_fwd_tc": _events_ms(lambda: r.render(d["opacity"], "tc_fp16_split"), steps, warmup, flush),
+                  "render_fwd_fp32": _events_ms(lambda: r.render(d["opacity"], "fp32"), steps, warmup, flush)}}
     del r
     torch.cuda.empty_cache()
     return out
@@ -510,9 +532,11 @@ def run_tcgs(args):
     probe = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], dsc["sh_degree"])
     n_splats = int(probe["tiles_touched"].to(torch.int64).sum().item())
     capacity = n_splats + 1024
-    r = tc.Renderer(cam, P, capacity, device=dev, stats=True)
+    exact = args.coverage == "exact"
+    r = tc.Renderer(cam, P, capacity, device=dev, stats=True, exact_tiles=exact)
     r.frame(dsc, precision="fp32")
     torch.cuda.synchronize()
+    n_binned = int(r.bins["n_splats"].item())
     st = r.stats.to(torch.int64).sum(dim=0).tolist()
     f_blend, f_cull, slots_fp32 = st[0], st[1], st[2]
     alpha_evals = f_blend + f_cull
@@ -608,9 +632,28 @@ def run_tcgs(args):
             acc[f"within_2e-3_{name}"] = float((np.abs(d).max(axis=0) <= 2e-3).mean())
             acc[f"max_abs_{name}"] = float(np.abs(d).max())
         acc["oracle_pixels_compared"] = int(mask.sum())
-    ablation = tight = None
+    ablation = tight = other = None
     if not args.no_extras:
-        ablation = bench_ablation(r, dsc, flush, img_fp32, oimg, mask)
+        # the same frame binned with the other coverage rule, both renderers; the ablation of Tables 4
+        # and 5 runs on the paper's lists (3-sigma squares)
+        r_o = tc.Renderer(cam, P, capacity, device=dev, exact_tiles=not exact)
+        r_o.frame(dsc, precision="fp32")
+        torch.cuda.synchronize()
+        other = {"coverage": "square" if exact else "exact", "splats": int(r_o.bins["n_splats"].item())}
+        img_o32 = r_o.out["img"].clone()
+        for prec in (args.precision, "fp32"):
+            tq, sq = time_frames(r_o, dsc, prec, args.steps, args.warmup, use_graph, flush, stream)
+            other[prec] = {"frames_per_s": 1000.0 / statistics.mean(tq),
+                           "stages_ms": dict(zip(["project", "bin_sort", "render_fwd"],
+                                                 [statistics.mean(x) for x in sq]))}
+        r_o.frame(dsc, precision=args.precision)
+        torch.cuda.synchronize()
+        other["images_equal_headline"] = {args.precision: bool(torch.equal(r_o.out["img"], img_tc)),
+                                          "fp32": bool(torch.equal(img_o32, img_fp32))}
+        r_sq = r_o if exact else r
+        r_sq.frame(dsc, precision="fp32")
+        ablation = bench_ablation(r_sq, dsc, flush, r_sq.out["img"].clone(), oimg, mask)
+        del r_o, r_sq
         tight = bench_tight_radius(cam, sc, dsc, dev, flush, with_oracle=not args.no_cpu_baseline)
 
     # --- roofline of the dominant kernel
@@ -629,7 +672,7 @@ def run_tcgs(args):
     rl_render["tensor_frac"] = rl_render["tensor_tflops"] / rl_render["tensor_peak_tflops"]
     tile_bits = max(1, math.ceil(math.log2(r.num_tiles)))
     tpasses = 1 if tile_bits <= 8 else (2 if tile_bits <= 16 else 3)
-    bin_bytes = P * (4 * 20 + 8 + 24) + n_splats * (8 + tpasses * 20 + 8)
+    bin_bytes = P * (4 * 20 + 8 + 24) + n_binned * (8 + tpasses * 20 + 8)
     rl_bin = {"bound": "hbm", "achieved": bin_bytes / (stage_ms[1] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
               "unit": "GB/s", "traffic": None, "kernel": "tcgs_bin_sort (whole stage)",
               "peak_source": peak_src}
@@ -658,7 +701,8 @@ def run_tcgs(args):
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f16 tensor-core exponent, f32 accumulate and blend", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "P": P, "splats": n_splats, "precision": args.precision,
+        "config": {"workload": WORKLOAD, "P": P, "splats": n_binned, "splats_3sigma_square": n_splats,
+                   "coverage": args.coverage, "precision": args.precision,
                    "l2": "flushed (256 MB write) between timed steps, outside the events",
                    "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "single GPU"},
         "alpha_evals_per_frame": alpha_evals, "f_blend": f_blend, "f_cull": f_cull,
@@ -679,6 +723,7 @@ def run_tcgs(args):
         "workloads": extras,
         "ablation": ablation,
         "tight_radius": tight,
+        "other_coverage": other,
     }
     print(json.dumps(line))
     if world > 1:

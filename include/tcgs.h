@@ -180,6 +180,27 @@ TCGS_API tcgs_status tcgs_bin_sort(const tcgs_camera* cam /* host */, int32_t P,
                           void* workspace, size_t ws_bytes, uint32_t* ids_sorted, uint32_t* tile_ranges,
                           int64_t* n_splats, int32_t* status, tcgs_stream stream);
 
+/*
+ * tcgs_bin_sort with exact tile coverage.  The paper leaves the Gaussian-tile coverage test to the
+ * implementation (Sec. 3.1: it "depends on the specific algorithm"; Sec. 2 cites methods that cut
+ * the Gaussian-tile pairs).  Here splat (g, t) is made only when t lies in g's rectangle (as for
+ * tcgs_bin_sort) AND g can reach alpha >= 1/255 (Eq. 5) at some pixel centre of t:
+ *   min over the pixel-centre box of t of (m - p)^T Q (m - p)  <=  L(o),
+ *   L(o) = 2 (ln o + ln 255) (1 + 1e-4) + 1e-3   (no tile when 2 (ln o + ln 255) <= -1e-3),
+ * with m = mean2d[g], Q = the conic of g, o = opacity[g], evaluated in FP32 (the minimum over the
+ * box in tile-local coordinates, in closed form: 0 when m is inside, else the least of the four edge
+ * minima).  A dropped splat is culled at every pixel of its tile by Algorithm 1, and the margins make
+ * that hold for the FP32 and tensor-core renderers' own arithmetic too, so every image rendered from
+ * these lists equals the image rendered from tcgs_bin_sort's (only list positions, and so
+ * n_contrib, differ).  Order, ranges, outputs, workspace and status as tcgs_bin_sort.
+ * In:  conic [P,3], opacity [P] (post-sigmoid) as given to the renderer; both non-null when P > 0.
+ */
+TCGS_API tcgs_status tcgs_bin_sort_exact(const tcgs_camera* cam /* host */, int32_t P, const float* mean2d,
+                                         const int32_t* radius, const float* depth, const float* conic,
+                                         const float* opacity, int64_t splat_capacity, void* workspace,
+                                         size_t ws_bytes, uint32_t* ids_sorted, uint32_t* tile_ranges,
+                                         int64_t* n_splats, int32_t* status, tcgs_stream stream);
+
 /* Size of the scratch array built into the library for tcgs_bin_sort_noalloc (64 MiB). */
 #define TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

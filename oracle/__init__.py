@@ -68,10 +68,13 @@ def _L():
             lib.orc_quat_to_rot.argtypes = [P(d), P(d)]
             lib.orc_project.argtypes = [cam, ctypes.c_int, ctypes.c_int] + [P(d)] * 5 + [ctypes.c_int] + \
                 [P(d), P(d), P(d), P(i32), P(d), P(i32), P(d)]
-            lib.orc_count_splats.argtypes = [cam, ctypes.c_int, P(d), P(i32)]
+            lib.orc_count_splats.argtypes = [cam, ctypes.c_int, P(d), P(i32), P(d), P(d)]
             lib.orc_count_splats.restype = i64
-            lib.orc_bin_sort.argtypes = [cam, ctypes.c_int, P(d), P(i32), P(d), i64, P(i32), P(i32), P(i32)]
+            lib.orc_bin_sort.argtypes = [cam, ctypes.c_int, P(d), P(i32), P(d), P(d), P(d), i64, P(i32), P(i32),
+                                         P(i32)]
             lib.orc_bin_sort.restype = i64
+            lib.orc_box_min_q.argtypes = [ctypes.c_double] * 9
+            lib.orc_box_min_q.restype = ctypes.c_double
             lib.orc_render.argtypes = [cam, d, P(i32), P(i32), P(d), P(d), P(d), P(d), P(d),
                                        P(d), P(d), P(i32), P(i32), P(d), P(d), P(i64), P(i32), ctypes.c_int]
             lib.orc_render_bruteforce.argtypes = [cam, d, ctypes.c_int, P(d), P(i32), P(d), P(d), P(d), P(d),
@@ -132,21 +135,31 @@ def grid(cam: dict):
     return (int(cam["width"]) + TILE - 1) // TILE, (int(cam["height"]) + TILE - 1) // TILE
 
 
-def bin_sort(cam: dict, mean2d, radius, depth) -> dict:
-    """Splats, per-tile depth order and tile ranges (Sec. 3.1, Eq. 3)."""
+def bin_sort(cam: dict, mean2d, radius, depth, conic=None, opacity=None) -> dict:
+    """Splats, per-tile depth order and tile ranges (Sec. 3.1, Eq. 3).  With conic and opacity,
+    exact coverage: a rectangle tile is kept only when the Gaussian reaches alpha >= 1/255 on the
+    tile's box of pixel centres (limit with margins, see tile_reached in the C oracle)."""
     c = camera(cam)
     mean2d = _f64(mean2d); radius = _i32(radius); depth = _f64(depth)
+    d = ctypes.c_double
+    cq = None if conic is None else _f64(conic)
+    op = None if conic is None else _f64(opacity)
     P = radius.shape[0]
     gw, gh = grid(cam)
-    n = _L().orc_count_splats(ctypes.byref(c), P, _p(mean2d, ctypes.c_double), _p(radius, ctypes.c_int32))
+    n = _L().orc_count_splats(ctypes.byref(c), P, _p(mean2d, d), _p(radius, ctypes.c_int32), _p(cq, d), _p(op, d))
     ids = np.zeros(max(n, 1), np.int32)
     tiles = np.zeros(max(n, 1), np.int32)
     ranges = np.zeros(2 * gw * gh, np.int32)
-    got = _L().orc_bin_sort(ctypes.byref(c), P, _p(mean2d, ctypes.c_double), _p(radius, ctypes.c_int32),
-                            _p(depth, ctypes.c_double), n, _p(ids, ctypes.c_int32), _p(tiles, ctypes.c_int32),
+    got = _L().orc_bin_sort(ctypes.byref(c), P, _p(mean2d, d), _p(radius, ctypes.c_int32), _p(cq, d), _p(op, d),
+                            _p(depth, d), n, _p(ids, ctypes.c_int32), _p(tiles, ctypes.c_int32),
                             _p(ranges, ctypes.c_int32))
     assert got == n
     return dict(n=int(n), ids=ids[:n], tile_of=tiles[:n], ranges=ranges.reshape(-1, 2))
+
+
+def box_min_q(mx, my, a, b, c, x0, x1, y0, y1) -> float:
+    """Least value of the conic form (x - m)^T Q (x - m) over a box (the exact-coverage test)."""
+    return float(_L().orc_box_min_q(mx, my, a, b, c, x0, x1, y0, y1))
 
 
 def render(cam: dict, binned: dict, mean2d, conic, opacity, rgb, bg=(0.0, 0.0, 0.0), alpha_max=0.99,

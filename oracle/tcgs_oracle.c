@@ -16,7 +16,9 @@
  *   - mean2d = (fx * X / Z + cx, fy * Y / Z + cy) in camera coordinates;
  *   - a Gaussian covers tile (tx, ty) iff the axis-aligned square
  *     [mx - r, mx + r] x [my - r, my + r] meets the tile's pixel square
- *     [16 tx, 16 tx + 16) x [16 ty, 16 ty + 16);
+ *     [16 tx, 16 tx + 16) x [16 ty, 16 ty + 16); with exact coverage it must
+ *     also reach alpha >= 1/255 (Eq. 5) somewhere on the tile's box of pixel
+ *     centres, with the margins stated at tile_reached();
  *   - alpha is clamped to alpha_max (0.99 in the official 3DGS renderer that
  *     the paper builds on; alpha_max = 1 reproduces Algorithm 1 literally);
  *   - the termination test of Algorithm 1 is T - alpha * T < 1e-4, evaluated
@@ -241,40 +243,101 @@ static int cmp_splat(const void* pa, const void* pb)
     return 0;
 }
 
-int64_t orc_count_splats(const orc_camera* cam, int P, const double* mean2d, const int32_t* radius)
+/* Least value of q(x, y) = a (x - mx)^2 + 2 b (x - mx)(y - my) + c (y - my)^2 (Q = [[a, b], [b, c]]
+ * positive definite) over the box [x0, x1] x [y0, y1].  The unconstrained minimiser is (mx, my);
+ * when it lies outside the box the minimum is on the boundary, and on each edge q is a parabola in
+ * the free coordinate: on x = X it is least at y = my - b (X - mx) / c, on y = Y at
+ * x = mx - b (Y - my) / a, each clamped to the edge. */
+double orc_box_min_q(double mx, double my, double a, double b, double c, double x0, double x1, double y0, double y1)
+{
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.0;
+    double best = INFINITY;
+    const double xs[2] = {x0, x1}, ys[2] = {y0, y1};
+    for (int e = 0; e < 2; ++e) {
+        double X = xs[e];
+        double y = my - b * (X - mx) / c;
+        if (y < y0) y = y0;
+        if (y > y1) y = y1;
+        double dx = X - mx, dy = y - my;
+        double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
+        if (q < best) best = q;
+        double Y = ys[e];
+        double x = mx - b * (Y - my) / a;
+        if (x < x0) x = x0;
+        if (x > x1) x = x1;
+        dx = x - mx; dy = Y - my;
+        q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
+        if (q < best) best = q;
+    }
+    return best;
+}
+
+/* Exact coverage: alpha = o exp(-q / 2) >= 1/255 (Eq. 5) needs q <= 2 (ln o + ln 255); the limit
+ * adds a relative margin of 1e-4 and an absolute one of 1e-3 (so that no splat that some FP32
+ * evaluation could keep is dropped), and no tile qualifies when 2 (ln o + ln 255) <= -1e-3. */
+static double reach_limit(double o)
+{
+    double reach = 2.0 * (log(o) + log(255.0));
+    return reach > -1e-3 ? reach * 1.0001 + 1e-3 : -1.0;
+}
+
+static int tile_reached(int tx, int ty, double mx, double my, const double* q, double o)
+{
+    double lim = reach_limit(o);
+    if (lim < 0.0) return 0;
+    double x0 = ORC_TILE * tx + 0.5, y0 = ORC_TILE * ty + 0.5;
+    return orc_box_min_q(mx, my, q[0], q[1], q[2], x0, x0 + ORC_TILE - 1, y0, y0 + ORC_TILE - 1) <= lim;
+}
+
+/* Splats of Gaussian g: its rectangle's tiles, or with conic and opacity given (exact coverage)
+ * those of them it reaches.  tiles (nullable) receives the tile ids in row-major order. */
+static int64_t gaussian_tiles(const orc_camera* cam, int g, const double* mean2d, const int32_t* radius,
+                              const double* conic, const double* opacity, int32_t* tiles)
+{
+    if (radius[g] <= 0) return 0;
+    int x0, x1, y0, y1, gw = grid_w(cam);
+    if (tile_rect(cam, mean2d[2 * g], mean2d[2 * g + 1], radius[g], &x0, &x1, &y0, &y1) == 0) return 0;
+    int64_t n = 0;
+    for (int ty = y0; ty <= y1; ++ty)
+        for (int tx = x0; tx <= x1; ++tx) {
+            if (conic && !tile_reached(tx, ty, mean2d[2 * g], mean2d[2 * g + 1], conic + 3 * g, opacity[g]))
+                continue;
+            if (tiles) tiles[n] = ty * gw + tx;
+            ++n;
+        }
+    return n;
+}
+
+int64_t orc_count_splats(const orc_camera* cam, int P, const double* mean2d, const int32_t* radius,
+                         const double* conic, const double* opacity)
 {
     int64_t n = 0;
-    for (int g = 0; g < P; ++g) {
-        if (radius[g] <= 0) continue;
-        int x0, x1, y0, y1;
-        n += tile_rect(cam, mean2d[2 * g], mean2d[2 * g + 1], radius[g], &x0, &x1, &y0, &y1);
-    }
+    for (int g = 0; g < P; ++g) n += gaussian_tiles(cam, g, mean2d, radius, conic, opacity, NULL);
     return n;
 }
 
 /* ids_sorted[N], tile_of[N] (nullable), ranges[2 * num_tiles] = [start, end). */
 int64_t orc_bin_sort(const orc_camera* cam, int P, const double* mean2d, const int32_t* radius,
-                     const double* depth, int64_t capacity, int32_t* ids_sorted, int32_t* tile_of,
-                     int32_t* ranges)
+                     const double* conic, const double* opacity, const double* depth, int64_t capacity,
+                     int32_t* ids_sorted, int32_t* tile_of, int32_t* ranges)
 {
     int gw = grid_w(cam), gh = grid_h(cam);
-    int64_t n = orc_count_splats(cam, P, mean2d, radius);
+    int64_t n = orc_count_splats(cam, P, mean2d, radius, conic, opacity);
     for (int t = 0; t < 2 * gw * gh; ++t) ranges[t] = 0;
     if (n > capacity) return -n;
     orc_splat* sp = (orc_splat*)malloc(sizeof(orc_splat) * (size_t)(n > 0 ? n : 1));
+    int32_t* tl = (int32_t*)malloc(sizeof(int32_t) * (size_t)gw * (size_t)gh);
     int64_t k = 0;
     for (int g = 0; g < P; ++g) {
-        if (radius[g] <= 0) continue;
-        int x0, x1, y0, y1;
-        if (tile_rect(cam, mean2d[2 * g], mean2d[2 * g + 1], radius[g], &x0, &x1, &y0, &y1) == 0) continue;
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) {
-                sp[k].tile = ty * gw + tx;
-                sp[k].depth = depth[g];
-                sp[k].id = g;
-                ++k;
-            }
+        int64_t m = gaussian_tiles(cam, g, mean2d, radius, conic, opacity, tl);
+        for (int64_t j = 0; j < m; ++j) {
+            sp[k].tile = tl[j];
+            sp[k].depth = depth[g];
+            sp[k].id = g;
+            ++k;
+        }
     }
+    free(tl);
     qsort(sp, (size_t)n, sizeof(orc_splat), cmp_splat);
     for (int64_t s = 0; s < n; ++s) {
         ids_sorted[s] = sp[s].id;

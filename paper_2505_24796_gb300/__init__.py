@@ -25,6 +25,7 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_GLOBAL, TCG
 TILE = 16
 
 __all__ = ["tcgs_project", "tcgs_project_bwd", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
+           "tcgs_bin_sort_exact",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
            "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
@@ -132,7 +133,9 @@ def tcgs_bin_sort_workspace_size(P: int, capacity: int, num_tiles: int) -> int:
     return int(_L().tcgs_bin_sort_workspace_size(int(P), int(capacity), int(num_tiles)))
 
 
-def tcgs_bin_sort(cam, mean2d, radius, depth, capacity: int, workspace=None, out=None, stream=None) -> dict:
+def tcgs_bin_sort(cam, mean2d, radius, depth, capacity: int, workspace=None, out=None, stream=None, conic=None,
+                  opacity=None) -> dict:
+    """Sorting stage.  With conic and opacity given, tcgs_bin_sort_exact (exact tile coverage)."""
     c = _cam(cam)
     P = mean2d.shape[0]
     dev = mean2d.device
@@ -146,13 +149,23 @@ def tcgs_bin_sort(cam, mean2d, radius, depth, capacity: int, workspace=None, out
                    tile_ranges=torch.empty(nt, 2, dtype=torch.int32, device=dev),
                    n_splats=torch.empty(1, dtype=torch.int64, device=dev),
                    status=torch.empty(1, dtype=torch.int32, device=dev))
-    check("tcgs_bin_sort", _L().tcgs_bin_sort(
-        ctypes.byref(c), P, _ptr(mean2d, torch.float32, "mean2d"), _ptr(radius, torch.int32, "radius"),
-        _ptr(depth, torch.float32, "depth"), int(capacity), _ptr(workspace, None, "workspace"),
-        workspace.numel() * workspace.element_size(), _ptr(out["ids_sorted"], torch.int32),
-        _ptr(out["tile_ranges"], torch.int32), _ptr(out["n_splats"], torch.int64), _ptr(out["status"], torch.int32),
-        _stream(stream)))
+    tail = (int(capacity), _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(),
+            _ptr(out["ids_sorted"], torch.int32), _ptr(out["tile_ranges"], torch.int32),
+            _ptr(out["n_splats"], torch.int64), _ptr(out["status"], torch.int32), _stream(stream))
+    head = (ctypes.byref(c), P, _ptr(mean2d, torch.float32, "mean2d"), _ptr(radius, torch.int32, "radius"),
+            _ptr(depth, torch.float32, "depth"))
+    if conic is None:
+        check("tcgs_bin_sort", _L().tcgs_bin_sort(*head, *tail))
+    else:
+        check("tcgs_bin_sort_exact", _L().tcgs_bin_sort_exact(*head, _ptr(conic, torch.float32, "conic"),
+                                                              _ptr(opacity, torch.float32, "opacity"), *tail))
     return out
+
+
+def tcgs_bin_sort_exact(cam, mean2d, radius, depth, conic, opacity, capacity: int, workspace=None, out=None,
+                        stream=None) -> dict:
+    """tcgs_bin_sort_exact: splats only for the tiles each Gaussian reaches with alpha >= 1/255."""
+    return tcgs_bin_sort(cam, mean2d, radius, depth, capacity, workspace, out, stream, conic=conic, opacity=opacity)
 
 
 def tcgs_bin_sort_noalloc(cam, mean2d, radius, depth, capacity: int, out=None, stream=None) -> dict:
@@ -335,10 +348,15 @@ class Renderer:
     """Preallocated buffers for one camera, scene size and splat capacity; ``frame`` runs
     project -> bin_sort -> render_fwd on the current stream with no host synchronisation."""
 
-    def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False, tight_radius: bool = False):
-        """tight_radius: bin with the opacity-aware coverage square instead of the 3-sigma one."""
+    def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False, tight_radius: bool = False,
+                 exact_tiles: bool = False):
+        """tight_radius: bin with the opacity-aware coverage square instead of the 3-sigma one.
+        exact_tiles: keep only the tiles each Gaussian reaches with alpha >= 1/255
+        (tcgs_bin_sort_exact; the same images, shorter lists)."""
         self.cam = _cam(cam)
         self.tight_radius = bool(tight_radius)
+        self.exact_tiles = bool(exact_tiles)
+        self.opacity = None
         self.P, self.capacity = int(P), int(capacity)
         dev = torch.device(device)
         gw, gh = grid(self.cam)
@@ -360,13 +378,20 @@ class Renderer:
         self.device_status = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def project(self, scene: dict, stream=None):
+        self.opacity = scene["opacity"]
         return tcgs_project(self.cam, scene["means3"], scene["scales"], scene["quats"], scene["sh"],
                             scene["sh_degree"], out=self.proj, stream=stream,
                             opacity=scene["opacity"] if self.tight_radius else None)
 
-    def bin_sort(self, stream=None):
+    def bin_sort(self, stream=None, opacity=None):
+        """opacity: the scene's (exact_tiles only; default the one the last project() saw)."""
+        exact = self.exact_tiles
+        op = (opacity if opacity is not None else self.opacity) if exact else None
+        if exact and op is None:
+            raise ValueError("exact_tiles binning needs the opacities: call project() first or pass opacity")
         return tcgs_bin_sort(self.cam, self.proj["mean2d"], self.proj["radius"], self.proj["depth"], self.capacity,
-                             workspace=self.ws, out=self.bins, stream=stream)
+                             workspace=self.ws, out=self.bins, stream=stream,
+                             conic=self.proj["conic"] if exact else None, opacity=op)
 
     def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=None, bg=(0, 0, 0),
                stream=None, tile_cull=True):
@@ -432,7 +457,7 @@ class _Project(torch.autograd.Function):
 
 
 def render_gaussians(cam, means3, scales, quats, opacity, sh, sh_degree, precision="tc_fp16_split", alpha_max=0.99,
-                     bg=(0.0, 0.0, 0.0), tight_radius=False, capacity=None):
+                     bg=(0.0, 0.0, 0.0), tight_radius=False, capacity=None, exact_tiles=False):
     """Differentiable frame from 3D Gaussians: project -> bin_sort -> render.  Gradients flow to
     means3, scales, quats, opacity and sh through tcgs_render_bwd and tcgs_project_bwd (binning is
     piecewise constant).  Returns (img [3,H,W], T_final [H,W]).  capacity None sizes the splat
@@ -442,6 +467,8 @@ def render_gaussians(cam, means3, scales, quats, opacity, sh, sh_degree, precisi
                                                               opacity.detach() if tight_radius else None)
     if capacity is None:
         capacity = int(tiles.to(torch.int64).sum().item()) + 1
-    bins = tcgs_bin_sort(c, mean2d.detach(), radius, depth, capacity)
+    bins = tcgs_bin_sort(c, mean2d.detach(), radius, depth, capacity,
+                         conic=conic.detach() if exact_tiles else None,
+                         opacity=opacity.detach() if exact_tiles else None)
     return rasterize(mean2d, conic, opacity, rgb, c, bins["tile_ranges"], bins["ids_sorted"], precision, alpha_max,
                      bg)

@@ -58,6 +58,7 @@ SIGNATURES = {
     "tcgs_bin_sort_workspace_size": (c_size_t, [c_int32, c_int64, c_int32]),
     "tcgs_bin_sort": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
     "tcgs_bin_sort_noalloc": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, V, V, V, V]),
+    "tcgs_bin_sort_exact": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
     "tcgs_render_fwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_render_bwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_render_fwd_batched": (c_int32, [c_int32, V, P_OPT, V, V, V, c_int32, V, c_int32, V]),

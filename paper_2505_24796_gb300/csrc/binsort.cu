@@ -227,22 +227,177 @@ __device__ __forceinline__ uint32_t orderable_bits(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// Exact tile coverage (tcgs_bin_sort_exact): Gaussian g reaches tile t when the least value of its
+// conic form over t's 16 x 16 box of pixel centres, in tile-local coordinates, is at most its reach
+// limit (the TC renderer's block-mark limit, whose boxes lie inside the tile's).  Per warp, the 32
+// Gaussians' parameters are staged in shared memory once; every splat then reads its Gaussian's.
+struct Cover {
+    float mx, my, a, b, c, ia, ic, lim;
+};
+
+__device__ __forceinline__ Cover cover_of(const float* __restrict__ mean2d, const float* __restrict__ conic,
+                                          const float* __restrict__ opacity, uint32_t g) {
+    Cover v;
+    const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
+    v.mx = m.x; v.my = m.y;
+    v.a = conic[3 * g]; v.b = conic[3 * g + 1]; v.c = conic[3 * g + 2];
+    v.lim = reach_limit(__logf(opacity[g]));
+    v.ia = __fdividef(1.f, v.a);
+    v.ic = __fdividef(1.f, v.c);
+    return v;
+}
+
+// Least value of the conic form over the tile's pixel-centre box [-h, h]^2 (tile-local mean lx, ly):
+// 0 when the mean is inside; otherwise on the edges facing the mean (a vertical one when the mean is
+// left or right of the box, a horizontal one when it is above or below), each minimised at its
+// clamped stationary point -- the same values min_q_box_r computes for those edges; the edges
+// facing away cannot hold the minimum of a convex form whose minimiser lies beyond the other side.
+__device__ __forceinline__ bool tile_reached(const Cover& v, float lx, float ly) {
+    constexpr float h = 0.5f * (kTile - 1);
+    if (!(v.lim >= 0.f)) return false;
+    const bool out_x = fabsf(lx) > h, out_y = fabsf(ly) > h;
+    if (!out_x && !out_y) return true;
+    float best = __int_as_float(0x7f800000);
+    if (out_x) {
+        const float X = lx > 0.f ? h : -h;
+        const float dx = lx - X;
+        const float y = fminf(h, fmaxf(-h, ly + v.b * dx * v.ic));
+        const float dy = ly - y;
+        best = fminf(best, v.a * dx * dx + 2.f * v.b * dx * dy + v.c * dy * dy);
+    }
+    if (out_y) {
+        const float Y = ly > 0.f ? h : -h;
+        const float ey = ly - Y;
+        const float x = fminf(h, fmaxf(-h, lx + v.b * ey * v.ia));
+        const float ex = lx - x;
+        best = fminf(best, v.a * ex * ex + 2.f * v.b * ex * ey + v.c * ey * ey);
+    }
+    return best <= v.lim;
+}
+
+// Owner of splat `sidx` among the warp's lanes, from the lanes' exclusive prefix `pre` of splat
+// counts: the last lane whose prefix is <= sidx (lanes with zero count share a prefix with the next
+// lane and are skipped because the search keeps the largest such lane).
+__device__ __forceinline__ int splat_owner(uint32_t pre, uint32_t sidx) {
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int cand = owner + step;
+        const uint32_t pv = __shfl_sync(0xffffffffu, pre, cand & 31);
+        if (cand < 32 && pv <= sidx) owner = cand;
+    }
+    return owner;
+}
+
+// Exact coverage, block-cooperative: the kThreads Gaussians of a block (thread t: Gaussian g_t) have
+// their rectangles' tiles dealt out over all threads, kThreads splats per round in Gaussian-major,
+// row-major order (so a Gaussian with thousands of tiles is spread over the whole block), and the
+// passing splats of each round are packed by a block scan.
+struct BlockCover {
+    Cover cv[kThreads];
+    uint4 rect[kThreads];        // x0, y0, width, exclusive prefix of the rectangle sizes
+    uint32_t cnt[kThreads];      // rectangle sizes
+    uint32_t wsum[kWarps];
+    uint32_t total;
+};
+
+// Stages thread t's Gaussian g (valid) and returns its rectangle size; sets bc.total.
+__device__ __forceinline__ uint32_t stage_block_cover(BlockCover& bc, const DevCamera& cam, bool valid, uint32_t g,
+                                                      const float* __restrict__ mean2d,
+                                                      const int32_t* __restrict__ radius,
+                                                      const float* __restrict__ conic,
+                                                      const float* __restrict__ opacity) {
+    const int t = threadIdx.x;
+    uint32_t cnt = 0, x0 = 0, y0 = 0, rw = 1;
+    Cover cv{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1.f};
+    if (valid) {
+        const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
+        const Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
+        cnt = rect_count(rc);
+        if (cnt) {
+            x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
+            cv = cover_of(mean2d, conic, opacity, g);
+        }
+    }
+    uint32_t total;
+    const uint32_t pre = block_exclusive_scan<uint32_t, kThreads>(cnt, bc.wsum, total);
+    bc.cv[t] = cv;
+    bc.rect[t] = make_uint4(x0, y0, rw, pre);
+    bc.cnt[t] = cnt;
+    if (t == 0) bc.total = total;
+    __syncthreads();
+    return cnt;
+}
+
+// Calls f(pass, sidx, owner, kk, tile, ex) for every splat of the block (every thread, every round;
+// pass false past the end), ex = the number of passing splats before this one in the block's order.
+template <typename F>
+__device__ __forceinline__ void block_cover_splats(BlockCover& bc, uint32_t grid_w, F&& f) {
+    const int t = threadIdx.x;
+    const uint32_t total = bc.total;
+    uint32_t run = 0;
+    for (uint32_t s0 = 0; s0 < total; s0 += kThreads) {
+        const uint32_t sidx = s0 + (uint32_t)t;
+        const bool active = sidx < total;
+        // owner: the last thread whose prefix is <= sidx (binary search over the block's prefixes)
+        int owner = 0;
+#pragma unroll
+        for (int step = kThreads / 2; step > 0; step >>= 1)
+            if (bc.rect[owner + step].w <= sidx) owner += step;
+        const uint4 r = bc.rect[owner];
+        const uint32_t kk = active ? sidx - r.w : 0u;
+        const uint32_t ty = r.y + kk / r.z, tx = r.x + kk % r.z;
+        const Cover& v = bc.cv[owner];
+        const float lx = v.mx - (float)(tx * kTile + kTile / 2), ly = v.my - (float)(ty * kTile + kTile / 2);
+        const bool pass = active && tile_reached(v, lx, ly);
+        uint32_t round_total;
+        const uint32_t ex = block_exclusive_scan<uint32_t, kThreads>(pass ? 1u : 0u, bc.wsum, round_total);
+        f(pass, active, owner, kk, ty * grid_w + tx, run + ex);
+        run += round_total;
+    }
+}
+
+// Depth keys, per-Gaussian splat counts, range clearing and the digit totals of pass 0.  The count
+// is the rectangle's tile count, or with EXACT the number of its tiles that pass the coverage test
+// (the difference of the block's running pass count at the Gaussian's first and last splat).
+template <bool EXACT>
 __global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, const float* __restrict__ mean2d,
                                                        const int32_t* __restrict__ radius,
-                                                       const float* __restrict__ depth, uint32_t* __restrict__ keys,
+                                                       const float* __restrict__ depth,
+                                                       const float* __restrict__ conic,
+                                                       const float* __restrict__ opacity, uint32_t* __restrict__ keys,
                                                        uint32_t* __restrict__ vals, uint32_t* __restrict__ counts,
                                                        uint32_t* __restrict__ ranges, int n_range_words,
                                                        uint32_t* __restrict__ digit_total0) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0) digit_total0[threadIdx.x] = 0u;
     if (i < n_range_words) ranges[i] = 0u;
-    if (i >= P) return;
-    float2 m = reinterpret_cast<const float2*>(mean2d)[i];
-    Rect rc = tile_rect(m.x, m.y, radius[i], cam.grid_w, cam.grid_h);
-    uint32_t c = rect_count(rc);
-    counts[i] = c;
-    keys[i] = c ? orderable_bits(depth[i]) : 0xFFFFFFFFu;
-    vals[i] = (uint32_t)i;
+    if (!EXACT) {
+        if (i >= P) return;
+        const float2 m = reinterpret_cast<const float2*>(mean2d)[i];
+        const Rect rc = tile_rect(m.x, m.y, radius[i], cam.grid_w, cam.grid_h);
+        const uint32_t c = rect_count(rc);
+        counts[i] = c;
+        keys[i] = c ? orderable_bits(depth[i]) : 0xFFFFFFFFu;
+        vals[i] = (uint32_t)i;
+        return;
+    }
+    __shared__ BlockCover s_bc;
+    __shared__ uint32_t s_first[kThreads], s_last[kThreads];
+    if ((int)(blockIdx.x * blockDim.x) >= P) return;   // the whole block is past the end
+    const uint32_t cnt = stage_block_cover(s_bc, cam, i < P, (uint32_t)i, mean2d, radius, conic, opacity);
+    block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool active, int owner, uint32_t kk, uint32_t,
+                                                      uint32_t before) {
+        if (active && kk == 0) s_first[owner] = before;
+        if (active && kk + 1 == s_bc.cnt[owner]) s_last[owner] = before + (pass ? 1u : 0u);
+    });
+    __syncthreads();
+    if (i < P) {
+        const uint32_t c = cnt ? s_last[threadIdx.x] - s_first[threadIdx.x] : 0u;
+        counts[i] = c;
+        keys[i] = c ? orderable_bits(depth[i]) : 0xFFFFFFFFu;
+        vals[i] = (uint32_t)i;
+    }
 }
 
 // block sums of counts[order[i]] over contiguous ranges
@@ -299,31 +454,62 @@ __global__ void __launch_bounds__(kThreads) k_scan_final(const uint32_t* __restr
 }
 
 // Duplication in depth order, one warp per 32 consecutive depth-sorted Gaussians: their splats
-// occupy one contiguous output range, which the warp writes cooperatively (lane s writes splats
-// s, s + 32, ...), finding each splat's Gaussian by a 5-step shuffle search over the warp's
-// exclusive prefix of splat counts.  Writes are coalesced and big Gaussians do not serialise a thread.
+// occupy one contiguous output range, which the warp writes cooperatively (lane s takes splat s,
+// s + 32, ... of the warp's rectangles, found by a shuffle search over the warp's exclusive prefix
+// of rectangle sizes).  Writes are coalesced and big Gaussians do not serialise a thread.  With
+// EXACT, only the tiles that pass the coverage test are written, packed by a ballot in the same
+// order (the warp's range then holds exactly the counted splats).
+template <bool EXACT>
 __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t P, const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint32_t* __restrict__ counts,
                                                         const float* __restrict__ mean2d,
                                                         const int32_t* __restrict__ radius,
+                                                        const float* __restrict__ conic,
+                                                        const float* __restrict__ opacity,
                                                         uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ n_u32) {
-    if (*n_u32 == 0u) return;
+    const uint32_t n_total = *n_u32;
+    if (n_total == 0u) return;
     const int lane = threadIdx.x & 31;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t g = 0, cnt = 0, x0 = 0, y0 = 0, rw = 1, off = 0;
+    uint32_t g = 0, off = 0;
+    bool listed = false;
     if (i < P) {
         g = order[i];
-        cnt = counts[g];
         off = offsets[i];
-        if (cnt) {
-            const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
-            const Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
-            x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
-        }
+        listed = counts[g] != 0u;
     }
-    // warp exclusive prefix of the counts (the warp's splats are contiguous from lane 0's offset)
+    if (EXACT) {
+        // the block's Gaussians are consecutive in depth order, so its splats are contiguous from
+        // thread 0's offset; each round's passing splats are packed by a block scan
+        __shared__ BlockCover s_bc;
+        __shared__ uint32_t s_g[kThreads];
+        __shared__ uint32_t s_first;
+        if (blockIdx.x * blockDim.x >= P) return;   // the whole block is past the end
+        if (threadIdx.x == 0) s_first = off;
+        s_g[threadIdx.x] = g;
+        stage_block_cover(s_bc, cam, listed, g, mean2d, radius, conic, opacity);
+        const uint32_t first = s_first;
+        block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool, int owner, uint32_t, uint32_t tile,
+                                                          uint32_t before) {
+            const uint32_t pos = first + before;
+            if (pass && pos < n_total) {   // always below N: the counts came from the same test
+                tile_keys[pos] = tile;
+                vals[pos] = s_g[owner];
+            }
+        });
+        return;
+    }
+    const uint32_t out = __shfl_sync(0xffffffffu, off, 0);   // the warp's splats start at lane 0's offset
+    uint32_t cnt = 0, x0 = 0, y0 = 0, rw = 1;
+    if (listed) {
+        const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
+        const Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
+        cnt = rect_count(rc);
+        x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
+    }
+    // warp exclusive prefix of the rectangle sizes
     uint32_t pre = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -332,18 +518,9 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
     }
     const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
     pre -= cnt;
-    const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
     for (uint32_t s0 = 0; s0 < total; s0 += 32) {
         const uint32_t sidx = s0 + (uint32_t)lane;
-        // owner = last lane whose prefix is <= sidx (lanes with zero count share a prefix with the
-        // next lane and are skipped because the search keeps the largest such lane)
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int cand = owner + step;
-            const uint32_t pv = __shfl_sync(0xffffffffu, pre, cand & 31);
-            if (cand < 32 && pv <= sidx) owner = cand;
-        }
+        const int owner = splat_owner(pre, sidx);
         const uint32_t o_pre = __shfl_sync(0xffffffffu, pre, owner);
         const uint32_t o_g = __shfl_sync(0xffffffffu, g, owner);
         const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, owner);
@@ -352,8 +529,8 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
         if (sidx < total) {
             const uint32_t kk = sidx - o_pre;
             const uint32_t ty = o_y0 + kk / o_rw, tx = o_x0 + kk % o_rw;
-            tile_keys[first + sidx] = ty * (uint32_t)cam.grid_w + tx;
-            vals[first + sidx] = o_g;
+            tile_keys[out + sidx] = ty * (uint32_t)cam.grid_w + tx;
+            vals[out + sidx] = o_g;
         }
     }
 }
@@ -474,11 +651,14 @@ extern "C" size_t tcgs_bin_sort_workspace_size(int32_t P, int64_t splat_capacity
     return tcgs::layout(nullptr, P, splat_capacity).bytes;
 }
 
-extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, const int32_t* radius,
-                                     const float* depth, int64_t splat_capacity, void* workspace, size_t ws_bytes,
-                                     uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_splats,
-                                     int32_t* status, tcgs_stream stream) {
-    using namespace tcgs;
+namespace tcgs {
+namespace {
+
+// The sorting stage; `exact` selects the exact tile coverage (conic and opacity are then read).
+tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, const int32_t* radius,
+                     const float* depth, bool exact, const float* conic, const float* opacity,
+                     int64_t splat_capacity, void* workspace, size_t ws_bytes, uint32_t* ids_sorted,
+                     uint32_t* tile_ranges, int64_t* n_splats, int32_t* status, cudaStream_t s) {
     if (!valid_camera(cam) || P < 0 || splat_capacity < 0 || splat_capacity > (int64_t)0xFFFFFFFFu)
         return TCGS_ERR_INVALID;
     if (!tile_ranges || !n_splats || !status || (P > 0 && (!mean2d || !radius || !depth)) || !workspace ||
@@ -490,14 +670,17 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     const int num_tiles = dc.grid_w * dc.grid_h;
     Workspace w = layout((char*)workspace, P, splat_capacity);
     if (ws_bytes < w.bytes) return TCGS_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream;
 
     // keys, counts, range clearing, digit totals of pass 0
     int n_init = P > 2 * num_tiles ? P : 2 * num_tiles;
     if (n_init < kThreads) n_init = kThreads;
-    k_bin_keys<<<(n_init + kThreads - 1) / kThreads, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, w.dk_a, w.dv_a,
-                                                                       w.counts, tile_ranges, 2 * num_tiles,
-                                                                       w.digit_total);
+    const int kb_blocks = (n_init + kThreads - 1) / kThreads;
+    if (exact)
+        k_bin_keys<true><<<kb_blocks, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, conic, opacity, w.dk_a, w.dv_a,
+                                                       w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
+    else
+        k_bin_keys<false><<<kb_blocks, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
+                                                        w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 1. depth order (4 passes; the result returns to the a-buffers)
@@ -532,8 +715,13 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     uint32_t* kbuf[2] = {w.sk_a, w.sk_b};
     uint32_t* vbuf[2] = {ids_sorted, w.sv_b};
     int src = (tpasses & 1) ? 1 : 0;
-    k_duplicate<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts,
-                                                                  mean2d, radius, kbuf[src], vbuf[src], w.n_u32);
+    const int dup_blocks = (P + kThreads - 1) / kThreads;
+    if (exact)
+        k_duplicate<true><<<dup_blocks, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts, mean2d, radius,
+                                                         conic, opacity, kbuf[src], vbuf[src], w.n_u32);
+    else
+        k_duplicate<false><<<dup_blocks, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
+                                                          radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 4. stable sort by tile id, 8 bits per pass (an even split of the tile bits measured slower)
@@ -552,6 +740,27 @@ extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const fl
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
+}
+
+}  // namespace
+}  // namespace tcgs
+
+extern "C" tcgs_status tcgs_bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, const int32_t* radius,
+                                     const float* depth, int64_t splat_capacity, void* workspace, size_t ws_bytes,
+                                     uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_splats,
+                                     int32_t* status, tcgs_stream stream) {
+    return tcgs::bin_sort(cam, P, mean2d, radius, depth, false, nullptr, nullptr, splat_capacity, workspace, ws_bytes,
+                          ids_sorted, tile_ranges, n_splats, status, (cudaStream_t)stream);
+}
+
+extern "C" tcgs_status tcgs_bin_sort_exact(const tcgs_camera* cam, int32_t P, const float* mean2d,
+                                           const int32_t* radius, const float* depth, const float* conic,
+                                           const float* opacity, int64_t splat_capacity, void* workspace,
+                                           size_t ws_bytes, uint32_t* ids_sorted, uint32_t* tile_ranges,
+                                           int64_t* n_splats, int32_t* status, tcgs_stream stream) {
+    if (P > 0 && (!conic || !opacity)) return TCGS_ERR_INVALID;
+    return tcgs::bin_sort(cam, P, mean2d, radius, depth, true, conic, opacity, splat_capacity, workspace, ws_bytes,
+                          ids_sorted, tile_ranges, n_splats, status, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- work-queue ordering

@@ -76,6 +76,39 @@ __device__ __forceinline__ uint32_t rect_count(const Rect& r) {
     return (uint32_t)(r.x1 - r.x0 + 1) * (uint32_t)(r.y1 - r.y0 + 1);
 }
 
+// Smallest value of q(p) = (m - p)^T Q (m - p) over the rectangle [x0, x1] x [y0, y1] of pixel
+// centres, Q = [[a, b], [b, c]] positive definite, with ia = 1/a and ic = 1/c precomputed: 0 when m
+// is inside, otherwise the smallest of the four edge minima (each a 1-D convex quadratic minimised
+// at its clamped stationary point).
+__device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float b, float c, float ia, float ic,
+                                             float x0, float x1, float y0, float y1) {
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
+    float best = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float X = e ? x1 : x0;
+        const float dx = mx - X;
+        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
+        const float dy = my - y;
+        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+        const float Y = e ? y1 : y0;
+        const float ey = my - Y;
+        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
+        const float ex = mx - x;
+        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
+    }
+    return best;
+}
+
+// Reach limit of a Gaussian with ln-opacity lno: alpha = o exp(-q/2) >= 1/255 (Eq. 5) needs
+// q <= 2 (ln o + ln 255).  The relative and absolute margins keep every test built on it (the TC
+// renderer's block marks, the exact tile coverage of the sorting stage) conservative under FP32
+// rounding; -1 when no q qualifies.
+__device__ __forceinline__ float reach_limit(float lno) {
+    const float reach = 2.f * (lno - kBetaCull);
+    return reach > -1e-3f ? reach * 1.0001f + 1e-3f : -1.f;
+}
+
 // 2^x on the SFU (PTX ex2.approx.ftz.f32).
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;

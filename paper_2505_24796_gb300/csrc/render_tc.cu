@@ -271,30 +271,6 @@ __device__ __forceinline__ Slot load_slot(const ViewData& vd, const float* opaci
     return d;
 }
 
-// Smallest value of q(p) = (m - p)^T Q (m - p) over the rectangle [x0, x1] x [y0, y1] of pixel
-// centres, Q = [[a, b], [b, c]] positive definite, with ia = 1/a and ic = 1/c precomputed: 0 when m
-// is inside, otherwise the smallest of the four edge minima (each a 1-D convex quadratic minimised
-// at its clamped stationary point).
-__device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float b, float c, float ia, float ic,
-                                             float x0, float x1, float y0, float y1) {
-    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
-    float best = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float X = e ? x1 : x0;
-        const float dx = mx - X;
-        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
-        const float dy = my - y;
-        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
-        const float Y = e ? y1 : y0;
-        const float ey = my - Y;
-        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
-        const float ex = mx - x;
-        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
-    }
-    return best;
-}
-
 // kEarly: EarlyCull form of the cull test; kSplit: the default encoding (TC_FP16_SPLIT with G2L)
 // fixed at compile time, otherwise the encoding and frame come from p.
 template <bool kInspect, bool kStats, bool kQueue, bool kEarly, bool kSplit>
@@ -419,10 +395,7 @@ __global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
             } else if (d.valid) {
                 mx = d.mx - cx; my = d.my - cy;   // G2L mean
                 const float lno = __logf(d.o);
-                // alpha >= 1/255 somewhere needs q <= 2 (ln o + ln 255); relative and absolute
-                // margins keep every test conservative under FP32 rounding
-                const float reach = 2.f * (lno - kBetaCull);
-                lim = reach > -1e-3f ? reach * 1.0001f + 1e-3f : -1.f;
+                lim = reach_limit(lno);
                 if (lim >= 0.f) {
                     // V only for Gaussians that can reach the tile: ||dmu - dp||_Q >= sqrt(q0) -
                     // |dp| sqrt(lambda_max(Q)), |dp| <= 7.5 sqrt(2); their tile-local coefficients

@@ -69,6 +69,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.tcgs_render_fwd(ctypes.byref(cam), ctypes.byref(opts), *([V] * 10), None) == _lib.TCGS_ERR_INVALID
     assert lib.tcgs_bin_sort(ctypes.byref(cam), 10, V, V, V, 2 ** 33, V, 0, V, V, V, V, None) == \
         _lib.TCGS_ERR_INVALID
+    assert lib.tcgs_bin_sort_exact(ctypes.byref(cam), 10, V, V, V, V, V, 100, V, 0, V, V, V, V, None) == \
+        _lib.TCGS_ERR_INVALID   # conic and opacity required
 
 
 def test_build_targets_sm103a_only():

@@ -190,6 +190,113 @@ def test_bin_sort_long_lists(tc, depths):
     np.testing.assert_array_equal(out["tile_ranges"].cpu().numpy(), b["ranges"])
 
 
+def _borderline(cam, inp, g, t, rel=1e-4, absol=2e-3):
+    """Splat (g, t) whose exact-coverage decision sits within FP32 rounding of the limit."""
+    gw, _ = oracle.grid(cam)
+    tx, ty = t % gw, t // gw
+    m = inp["mean2d"][g].astype(np.float64)
+    s11, s12, s22 = inp["conic"][g].astype(np.float64)
+    o = float(inp["opacity"][g])
+    qmin = oracle.box_min_q(m[0], m[1], s11, s12, s22, 16 * tx + 0.5, 16 * tx + 15.5, 16 * ty + 0.5, 16 * ty + 15.5)
+    lim = 2 * (math.log(o) + math.log(255.0)) * 1.0001 + 1e-3
+    return abs(qmin - lim) <= rel * (abs(lim) + qmin) + absol
+
+
+@pytest.mark.parametrize("name,make", SMALL + [("diff_crop_320x180", lambda: scenes.differentiation(
+    P=20_000, width=320, height=180, seed=13)[:2])])
+def test_bin_sort_exact_matches_oracle(tc, name, make):
+    """Exact tile coverage: per tile, the GPU list equals the oracle's on the same FP32 inputs except
+    for splats whose decision lies within FP32 rounding of the limit (each checked, and rare)."""
+    cam, sc = make()
+    _, inp, b_rect, _ = oracle_frame(cam, sc, render=False)
+    b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"], conic=inp["conic"],
+                        opacity=inp["opacity"])
+    g = gpu_inputs(inp, b)
+    out = tc.tcgs_bin_sort(cam, g["mean2d"], g["radius"], g["depth"], capacity=b_rect["n"] + 5, conic=g["conic"],
+                           opacity=g["opacity"])
+    torch.cuda.synchronize()
+    assert int(out["status"].item()) == 0
+    n = int(out["n_splats"].item())
+    ids, ranges = out["ids_sorted"].cpu().numpy()[:n], out["tile_ranges"].cpu().numpy()
+    mism = 0
+    for t, ((s0, e0), (s1, e1)) in enumerate(zip(b["ranges"], ranges)):
+        lo, lg = list(b["ids"][s0:e0]), list(ids[s1:e1])
+        if lo == lg:
+            continue
+        diff = set(lo) ^ set(lg)
+        mism += len(diff)
+        assert all(_borderline(cam, inp, gg, t) for gg in diff), (name, t, diff)
+        keep = lambda l: [x for x in l if x not in diff]
+        assert keep(lo) == keep(lg), (name, t)
+    print(f"\n[exact bins] {name}: {n} splats (3-sigma: {b_rect['n']}), {mism} borderline differences")
+    assert mism <= max(2, 1e-4 * b["n"])
+    assert n < b_rect["n"]
+
+
+@pytest.mark.parametrize("precision", ["tc_fp16_split", "fp32"])
+def test_exact_tiles_render_the_same_image(tc, precision):
+    """Rendering from the exact lists gives the image and final transmittance of the 3-sigma lists
+    bit for bit (the dropped splats are culled at every pixel by the renderers' own arithmetic);
+    n_contrib names the same last blended Gaussian."""
+    cam, sc = scenes.precision(P=30_000, width=240, height=120, seed=12)
+    dsc = {k: to_torch(v, DEV) if isinstance(v, np.ndarray) else v for k, v in sc.items()}
+    pr_g = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], sc["sh_degree"])
+    cap = int(pr_g["tiles_touched"].to(torch.int64).sum().item()) + 1
+    res = {}
+    for exact in (False, True):
+        b = tc.tcgs_bin_sort(cam, pr_g["mean2d"], pr_g["radius"], pr_g["depth"], cap,
+                             conic=pr_g["conic"] if exact else None, opacity=dsc["opacity"] if exact else None)
+        o = tc.tcgs_render_fwd(cam, tc.render_opts(precision), b["tile_ranges"], b["ids_sorted"], pr_g["mean2d"],
+                               pr_g["conic"], dsc["opacity"], pr_g["rgb"])
+        torch.cuda.synchronize()
+        n = int(b["n_splats"].item())
+        res[exact] = dict(img=o["img"].cpu().numpy(), T=o["T_final"].cpu().numpy(),
+                          nc=o["n_contrib"].cpu().numpy(), ids=b["ids_sorted"].cpu().numpy()[:n],
+                          ranges=b["tile_ranges"].cpu().numpy(), n=n)
+    r, e = res[False], res[True]
+    assert e["n"] < r["n"]
+    np.testing.assert_array_equal(r["img"], e["img"])
+    np.testing.assert_array_equal(r["T"], e["T"])
+    gw, _ = oracle.grid(cam)
+    H, W = r["T"].shape
+    ys, xs = np.nonzero(r["nc"] > 0)
+    assert ((r["nc"] > 0) == (e["nc"] > 0)).all()
+    t = (ys // 16) * gw + xs // 16
+    last_r = r["ids"][r["ranges"][t, 0] + r["nc"][ys, xs] - 1]
+    last_e = e["ids"][e["ranges"][t, 0] + e["nc"][ys, xs] - 1]
+    np.testing.assert_array_equal(last_r, last_e)
+    print(f"\n[exact tiles] {precision}: splats {r['n']} -> {e['n']}")
+
+
+def test_bin_sort_exact_long_lists_and_ties(tc):
+    """Exact coverage on tiles with thousands of candidate splats and exact depth ties."""
+    cam = scenes.pinhole(100, 70, fx=100.0)
+    rng = np.random.default_rng(23)
+    P = 20_000
+    mean2d = f32(np.c_[rng.uniform(-10, 110, P), rng.uniform(-10, 80, P)])
+    radius = rng.integers(1, 48, P).astype(np.int32)
+    A = rng.standard_normal((P, 2, 2)) * (radius[:, None, None] / 3.0)
+    cov = A @ A.transpose(0, 2, 1) + 0.3 * np.eye(2)
+    inv = np.linalg.inv(cov)
+    conic = f32(np.c_[inv[:, 0, 0], inv[:, 0, 1], inv[:, 1, 1]])
+    opacity = f32(rng.uniform(0.002, 1.0, P))
+    depth = f32(rng.choice([1.0, 2.0, 3.0, 4.0], P))
+    inp = dict(mean2d=mean2d, conic=conic, opacity=opacity)
+    b = oracle.bin_sort(cam, mean2d, radius, depth, conic=conic, opacity=opacity)
+    out = tc.tcgs_bin_sort(cam, to_torch(mean2d, DEV), to_torch(radius, DEV), to_torch(depth, DEV), capacity=b["n"] + 64,
+                           conic=to_torch(conic, DEV), opacity=to_torch(opacity, DEV))
+    torch.cuda.synchronize()
+    n = int(out["n_splats"].item())
+    ids, ranges = out["ids_sorted"].cpu().numpy()[:n], out["tile_ranges"].cpu().numpy()
+    assert np.diff(b["ranges"], axis=1).max() > 2048
+    for t, ((s0, e0), (s1, e1)) in enumerate(zip(b["ranges"], ranges)):
+        lo, lg = list(b["ids"][s0:e0]), list(ids[s1:e1])
+        if lo != lg:
+            diff = set(lo) ^ set(lg)
+            assert all(_borderline(cam, inp, gg, t) for gg in diff), (t, diff)
+            assert [x for x in lo if x not in diff] == [x for x in lg if x not in diff]
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):

@@ -236,6 +236,100 @@ def test_binning_depth_ties_ordered_by_index():
     assert list(b["ids"]) == [1, 0, 2]
 
 
+# ---------------------------------------------------------------- exact tile coverage
+
+def test_box_min_matches_dense_sampling_and_bounded_optimiser():
+    """The closed-form least value of the conic form over a box against the minimum over a
+    dense grid of the box and against a bounded quasi-Newton solve."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(5)
+    for _ in range(60):
+        A = rng.standard_normal((2, 2))
+        Q = A @ A.T + rng.uniform(0.01, 0.5) * np.eye(2)
+        a, b, c = Q[0, 0], Q[0, 1], Q[1, 1]
+        x0, y0 = rng.uniform(-20, 20, 2)
+        x1, y1 = x0 + rng.uniform(0.5, 15), y0 + rng.uniform(0.5, 15)
+        m = rng.uniform(-40, 40, 2)
+        got = oracle.box_min_q(m[0], m[1], a, b, c, x0, x1, y0, y1)
+        xs, ys = np.meshgrid(np.linspace(x0, x1, 801), np.linspace(y0, y1, 801))
+        dx, dy = xs - m[0], ys - m[1]
+        grid_min = float((a * dx * dx + 2 * b * dx * dy + c * dy * dy).min())
+        assert got <= grid_min + 1e-9 * (1 + grid_min)
+        f = lambda p: float(Q[0, 0] * (p[0] - m[0]) ** 2 + 2 * Q[0, 1] * (p[0] - m[0]) * (p[1] - m[1])
+                            + Q[1, 1] * (p[1] - m[1]) ** 2)
+        best = min(minimize(f, np.array(s0), bounds=[(x0, x1), (y0, y1)], method="L-BFGS-B",
+                            options=dict(ftol=1e-15, gtol=1e-12)).fun
+                   for s0 in [(x0, y0), (x1, y1), ((x0 + x1) / 2, (y0 + y1) / 2)])
+        assert abs(got - best) <= 1e-6 * (1 + best)
+
+
+def _exact_case(seed, P=400, width=96, height=80):
+    cam, sc = scenes.plain_forward(P=P, width=width, height=height, seed=seed)
+    pr = oracle.project(cam, sc)
+    op = np.asarray(sc["opacity"], np.float64)
+    rect = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
+    exact = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"], conic=pr["conic"], opacity=op)
+    return cam, sc, pr, op, rect, exact
+
+
+def _tile_lists(b):
+    return [list(b["ids"][s:e]) for s, e in b["ranges"]]
+
+
+def _max_alpha_on_tile(cam, pr, op, g, t):
+    gw, _ = oracle.grid(cam)
+    tx, ty = t % gw, t // gw
+    ys, xs = np.meshgrid(16 * ty + np.arange(16) + 0.5, 16 * tx + np.arange(16) + 0.5, indexing="ij")
+    dx, dy = xs - pr["mean2d"][g, 0], ys - pr["mean2d"][g, 1]
+    s11, s12, s22 = pr["conic"][g]
+    return float((op[g] * np.exp(-0.5 * (s11 * dx * dx + 2 * s12 * dx * dy + s22 * dy * dy))).max())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_exact_coverage_drops_only_splats_culled_at_every_pixel(seed):
+    """Each tile's exact list is its 3-sigma list minus entries whose alpha is below 1/255 at all
+    256 pixel centres (brute force), in the same order; an entry that reaches 1/255 anywhere stays."""
+    cam, sc, pr, op, rect, exact = _exact_case(seed)
+    assert 0 < exact["n"] < rect["n"]
+    for t, (lr, le) in enumerate(zip(_tile_lists(rect), _tile_lists(exact))):
+        assert le == [g for g in lr if g in set(le)]          # a subsequence: order kept
+        for g in set(lr) - set(le):
+            assert _max_alpha_on_tile(cam, pr, op, g, t) < 1.0 / 255.0
+        for g in le:
+            if _max_alpha_on_tile(cam, pr, op, g, t) >= 1.0 / 255.0:
+                continue
+            # kept without reaching 1/255 at a pixel centre: only inside the box and margin slack
+            gw, _ = oracle.grid(cam)
+            tx, ty = t % gw, t // gw
+            s11, s12, s22 = pr["conic"][g]
+            qmin = oracle.box_min_q(pr["mean2d"][g, 0], pr["mean2d"][g, 1], s11, s12, s22, 16 * tx + 0.5,
+                                    16 * tx + 15.5, 16 * ty + 0.5, 16 * ty + 15.5)
+            assert qmin <= 2 * (math.log(op[g]) + math.log(255.0)) * 1.0001 + 1e-3
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_exact_coverage_renders_the_same_image(seed):
+    """Algorithm 1 over the exact lists gives the image and final transmittance of the 3-sigma
+    lists bit for bit; n_contrib counts the same last blended Gaussian in the shorter list."""
+    cam, sc, pr, op, rect, exact = _exact_case(seed)
+    o_r = oracle.render(cam, rect, pr["mean2d"], pr["conic"], op, pr["rgb"])
+    o_e = oracle.render(cam, exact, pr["mean2d"], pr["conic"], op, pr["rgb"])
+    np.testing.assert_array_equal(o_r["img"], o_e["img"])
+    np.testing.assert_array_equal(o_r["T"], o_e["T"])
+    gw, _ = oracle.grid(cam)
+    lr, le = _tile_lists(rect), _tile_lists(exact)
+    H, W = o_r["T"].shape
+    for y in range(H):
+        for x in range(W):
+            t = (y // 16) * gw + x // 16
+            nr, ne = o_r["n_contrib"][y, x], o_e["n_contrib"][y, x]
+            if nr == 0:
+                assert ne == 0
+            else:
+                assert le[t][ne - 1] == lr[t][nr - 1]
+    assert o_e["alpha_evals"] < o_r["alpha_evals"] and o_e["f_blend"] == o_r["f_blend"]
+
+
 # ---------------------------------------------------------------- rendering
 
 def _render_scene(cam, sc, alpha_max=0.99, bg=(0, 0, 0)):
