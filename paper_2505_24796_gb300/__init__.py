@@ -27,7 +27,7 @@ TILE = 16
 __all__ = ["tcgs_project", "tcgs_project_bwd", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
            "tcgs_bin_sort_exact",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
-           "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS",
+           "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS", "FramePipeline",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
            "TCGS_TC_TF32_GLOBAL"]
 
@@ -404,6 +404,70 @@ class Renderer:
         self.project(scene, stream)
         self.bin_sort(stream)
         return self.render(scene["opacity"], precision, stream=stream, **kw)
+
+
+class FramePipeline:
+    """Frames whose scene arrays start in pinned host memory and whose image ends there.
+
+    The host->device copy of a frame's scene runs on a copy stream into one of two device scene
+    buffers while the previous frame renders on the compute stream, and each image returns on a
+    third stream, so a stream of frames runs at the pace of the slowest of the three (on GB300 the
+    host link).  Every frame's copies are issued by ``submit``; ``synchronize`` waits for all.
+
+      pipe = FramePipeline(renderer, precision="tc_fp16_split")
+      pipe.submit(host_scene, host_img)   # host tensors (pinned); returns at once
+      pipe.synchronize()
+    """
+
+    def __init__(self, renderer: "Renderer", precision="tc_fp16_split", **render_kw):
+        self.r = renderer
+        self.precision = precision
+        self.render_kw = render_kw
+        dev = renderer.out["img"].device
+        self.device = dev
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.d2h_stream = torch.cuda.Stream(device=dev)
+        self.compute_stream = torch.cuda.current_stream(dev)
+        self.scenes = [None, None]
+        self.outs = [renderer.out, {k: torch.empty_like(v) for k, v in renderer.out.items()}]
+        self.scene_free = [None, None]   # compute finished reading the slot's scene
+        self.out_free = [None, None]     # the slot's image has reached the host
+        self.n = 0
+
+    def _slot_scene(self, slot, host_scene):
+        if self.scenes[slot] is None:
+            self.scenes[slot] = {k: torch.empty(v.shape, dtype=v.dtype, device=self.device)
+                                 for k, v in host_scene.items() if isinstance(v, torch.Tensor)}
+            self.scenes[slot]["sh_degree"] = int(host_scene["sh_degree"])
+        return self.scenes[slot]
+
+    def submit(self, host_scene: dict, host_img: torch.Tensor):
+        slot = self.n & 1
+        dsc = self._slot_scene(slot, host_scene)
+        with torch.cuda.stream(self.copy_stream):
+            if self.scene_free[slot] is not None:
+                self.copy_stream.wait_event(self.scene_free[slot])
+            for k, v in host_scene.items():
+                if isinstance(v, torch.Tensor):
+                    dsc[k].copy_(v, non_blocking=True)
+            copied = self.copy_stream.record_event()
+        cs = self.compute_stream
+        cs.wait_event(copied)
+        if self.out_free[slot] is not None:
+            cs.wait_event(self.out_free[slot])
+        self.r.out = self.outs[slot]
+        out = self.r.frame(dsc, precision=self.precision, stream=None, **self.render_kw)
+        self.scene_free[slot] = cs.record_event()
+        with torch.cuda.stream(self.d2h_stream):
+            self.d2h_stream.wait_event(self.scene_free[slot])
+            host_img.copy_(out["img"], non_blocking=True)
+            self.out_free[slot] = self.d2h_stream.record_event()
+        self.n += 1
+        return out
+
+    def synchronize(self):
+        for s in (self.copy_stream, self.d2h_stream, self.compute_stream):
+            s.synchronize()
 
 
 # ---------------------------------------------------------------- autograd

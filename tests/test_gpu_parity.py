@@ -297,6 +297,33 @@ def test_bin_sort_exact_long_lists_and_ties(tc):
             assert [x for x in lo if x not in diff] == [x for x in lg if x not in diff]
 
 
+def test_frame_pipeline_matches_direct_frames(tc):
+    """FramePipeline (scene uploaded from pinned host memory while the previous frame renders, image
+    returned to the host) gives every frame's image bit for bit as a direct frame of that scene."""
+    cam, sc = scenes.plain_forward(P=1500, width=200, height=136, seed=11)
+    P = len(sc["opacity"])
+    cap = 4 * int(oracle.project(cam, scene64(sc))["tiles_touched"].sum()) + 64
+    variants = []
+    for f in (1.0, 0.4, 0.8, 0.25, 1.0):
+        v = {k: (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() if isinstance(x, np.ndarray) else x)
+             for k, x in sc.items()}
+        v["opacity"] = (v["opacity"] * f).pin_memory()
+        variants.append(v)
+    r = tc.Renderer(cam, P, cap, device=DEV)
+    pipe = tc.FramePipeline(r)
+    host = [torch.empty(3, cam["height"], cam["width"]).pin_memory() for _ in variants]
+    for v, h in zip(variants, host):
+        pipe.submit(v, h)
+    pipe.synchronize()
+    r2 = tc.Renderer(cam, P, cap, device=DEV)
+    for v, h in zip(variants, host):
+        d = {k: (x.to(DEV) if isinstance(x, torch.Tensor) else x) for k, x in v.items()}
+        out = r2.frame(d)
+        torch.cuda.synchronize()
+        assert torch.equal(out["img"].cpu(), h)
+    assert not torch.equal(host[0], host[1])
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
