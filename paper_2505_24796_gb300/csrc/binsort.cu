@@ -275,20 +275,6 @@ __device__ __forceinline__ bool tile_reached(const Cover& v, float lx, float ly)
     return best <= v.lim;
 }
 
-// Owner of splat `sidx` among the warp's lanes, from the lanes' exclusive prefix `pre` of splat
-// counts: the last lane whose prefix is <= sidx (lanes with zero count share a prefix with the next
-// lane and are skipped because the search keeps the largest such lane).
-__device__ __forceinline__ int splat_owner(uint32_t pre, uint32_t sidx) {
-    int owner = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int cand = owner + step;
-        const uint32_t pv = __shfl_sync(0xffffffffu, pre, cand & 31);
-        if (cand < 32 && pv <= sidx) owner = cand;
-    }
-    return owner;
-}
-
 // Exact coverage, block-cooperative: the kThreads Gaussians of a block (thread t: Gaussian g_t) have
 // their rectangles' tiles dealt out over all threads, kThreads splats per round in Gaussian-major,
 // row-major order (so a Gaussian with thousands of tiles is spread over the whole block), and the
@@ -301,7 +287,9 @@ struct BlockCover {
     uint32_t total;
 };
 
-// Stages thread t's Gaussian g (valid) and returns its rectangle size; sets bc.total.
+// Stages thread t's Gaussian g (valid) and returns its rectangle size; sets bc.total.  COVER: also
+// its coverage parameters (exact coverage).
+template <bool COVER = true>
 __device__ __forceinline__ uint32_t stage_block_cover(BlockCover& bc, const DevCamera& cam, bool valid, uint32_t g,
                                                       const float* __restrict__ mean2d,
                                                       const int32_t* __restrict__ radius,
@@ -316,12 +304,12 @@ __device__ __forceinline__ uint32_t stage_block_cover(BlockCover& bc, const DevC
         cnt = rect_count(rc);
         if (cnt) {
             x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
-            cv = cover_of(mean2d, conic, opacity, g);
+            if (COVER) cv = cover_of(mean2d, conic, opacity, g);
         }
     }
     uint32_t total;
     const uint32_t pre = block_exclusive_scan<uint32_t, kThreads>(cnt, bc.wsum, total);
-    bc.cv[t] = cv;
+    if (COVER) bc.cv[t] = cv;
     bc.rect[t] = make_uint4(x0, y0, rw, pre);
     bc.cnt[t] = cnt;
     if (t == 0) bc.total = total;
@@ -453,12 +441,12 @@ __global__ void __launch_bounds__(kThreads) k_scan_final(const uint32_t* __restr
     }
 }
 
-// Duplication in depth order, one warp per 32 consecutive depth-sorted Gaussians: their splats
-// occupy one contiguous output range, which the warp writes cooperatively (lane s takes splat s,
-// s + 32, ... of the warp's rectangles, found by a shuffle search over the warp's exclusive prefix
-// of rectangle sizes).  Writes are coalesced and big Gaussians do not serialise a thread.  With
-// EXACT, only the tiles that pass the coverage test are written, packed by a ballot in the same
-// order (the warp's range then holds exactly the counted splats).
+// Duplication in depth order, one block per 256 consecutive depth-sorted Gaussians: their splats
+// occupy one contiguous output range, which the block writes cooperatively, 256 splats per round
+// (thread t takes splat t of the round, its Gaussian found by a binary search over the block's
+// prefix of rectangle sizes).  Writes are coalesced and a Gaussian with thousands of tiles is spread
+// over the whole block.  With EXACT, only the tiles that pass the coverage test are written, packed
+// by a block scan in the same order (the block's range then holds exactly the counted splats).
 template <bool EXACT>
 __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t P, const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ offsets,
@@ -469,9 +457,11 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
                                                         const float* __restrict__ opacity,
                                                         uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ n_u32) {
+    __shared__ BlockCover s_bc;
+    __shared__ uint32_t s_g[kThreads];
+    __shared__ uint32_t s_first;
     const uint32_t n_total = *n_u32;
-    if (n_total == 0u) return;
-    const int lane = threadIdx.x & 31;
+    if (n_total == 0u || blockIdx.x * blockDim.x >= P) return;   // nothing to place, or past the end
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t g = 0, off = 0;
     bool listed = false;
@@ -480,15 +470,12 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
         off = offsets[i];
         listed = counts[g] != 0u;
     }
+    // the block's Gaussians are consecutive in depth order, so its splats are contiguous from
+    // thread 0's offset
+    if (threadIdx.x == 0) s_first = off;
+    s_g[threadIdx.x] = g;
     if (EXACT) {
-        // the block's Gaussians are consecutive in depth order, so its splats are contiguous from
-        // thread 0's offset; each round's passing splats are packed by a block scan
-        __shared__ BlockCover s_bc;
-        __shared__ uint32_t s_g[kThreads];
-        __shared__ uint32_t s_first;
-        if (blockIdx.x * blockDim.x >= P) return;   // the whole block is past the end
-        if (threadIdx.x == 0) s_first = off;
-        s_g[threadIdx.x] = g;
+        // each round's passing splats are packed by a block scan
         stage_block_cover(s_bc, cam, listed, g, mean2d, radius, conic, opacity);
         const uint32_t first = s_first;
         block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool, int owner, uint32_t, uint32_t tile,
@@ -501,37 +488,21 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
         });
         return;
     }
-    const uint32_t out = __shfl_sync(0xffffffffu, off, 0);   // the warp's splats start at lane 0's offset
-    uint32_t cnt = 0, x0 = 0, y0 = 0, rw = 1;
-    if (listed) {
-        const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
-        const Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
-        cnt = rect_count(rc);
-        x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
-    }
-    // warp exclusive prefix of the rectangle sizes
-    uint32_t pre = cnt;
+    // every rectangle tile is a splat: the block's splats fill [first, first + total) in order
+    stage_block_cover<false>(s_bc, cam, listed, g, mean2d, radius, conic, opacity);
+    const uint32_t first = s_first, total = s_bc.total;
+    for (uint32_t s0 = 0; s0 < total; s0 += kThreads) {
+        const uint32_t sidx = s0 + threadIdx.x;
+        if (sidx >= total) break;
+        int owner = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += y;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
-    pre -= cnt;
-    for (uint32_t s0 = 0; s0 < total; s0 += 32) {
-        const uint32_t sidx = s0 + (uint32_t)lane;
-        const int owner = splat_owner(pre, sidx);
-        const uint32_t o_pre = __shfl_sync(0xffffffffu, pre, owner);
-        const uint32_t o_g = __shfl_sync(0xffffffffu, g, owner);
-        const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, owner);
-        const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, owner);
-        const uint32_t o_rw = __shfl_sync(0xffffffffu, rw, owner);
-        if (sidx < total) {
-            const uint32_t kk = sidx - o_pre;
-            const uint32_t ty = o_y0 + kk / o_rw, tx = o_x0 + kk % o_rw;
-            tile_keys[out + sidx] = ty * (uint32_t)cam.grid_w + tx;
-            vals[out + sidx] = o_g;
-        }
+        for (int step = kThreads / 2; step > 0; step >>= 1)
+            if (s_bc.rect[owner + step].w <= sidx) owner += step;
+        const uint4 r = s_bc.rect[owner];
+        const uint32_t kk = sidx - r.w;
+        const uint32_t ty = r.y + kk / r.z, tx = r.x + kk % r.z;
+        tile_keys[first + sidx] = ty * (uint32_t)cam.grid_w + tx;
+        vals[first + sidx] = s_g[owner];
     }
 }
 
