@@ -310,7 +310,7 @@ def bench_scheduler(dev, train_views=200, chunk=16):
            "heldout_mse_log_cost": {"mlp": float(np.mean((pn - ytn) ** 2)), "list_length_fit": float(np.mean((base - ytn) ** 2))}}
     items = mv.items().cpu().numpy()
     cyc = dict(zip(items.tolist(), cycles.cpu().numpy().tolist()))
-    workers = 152 * 3
+    workers = 152 * 4   # resident CTAs of the persistent renderer
     times, sim = {}, {}
     for policy in ("natural", "length", "mlp"):
         q = mv.queue(policy, model)

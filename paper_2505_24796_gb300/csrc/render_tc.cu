@@ -55,8 +55,10 @@ constexpr int kSmemA = 0;              // U: 256 x 16 f16 = 8192 B (two 128-row 
 constexpr int kSmemB = 8192;           // V: 3 buffers
 constexpr int kSmemP = kSmemB + 3 * kVBytes;   // slot parameters and colours: 3 buffers
 // 46 KB of dynamic shared memory caps residency at 4 CTAs per SM (4 x 47 KB <= 228 KB < 5 x 47 KB),
-// so 4 x 128 TMEM columns always fit in the 512 available and tcgen05.alloc never waits
+// so 4 x 128 TMEM columns always fit in the 512 available and tcgen05.alloc never waits; the
+// launch bound (56 registers a thread) lets all 4 be resident
 constexpr int kSmemDyn = 46 * 1024;
+constexpr int kTcCtasPerSm = 4;
 constexpr float kCulledV = -30000.f;   // FP16-finite exponent of a slot that no pixel can use
 
 // Byte offset of the 16-byte chunk kchunk (K elements 8 kchunk .. 8 kchunk + 7) of row `row` of a
@@ -274,7 +276,7 @@ __device__ __forceinline__ Slot load_slot(const ViewData& vd, const float* opaci
 // kEarly: EarlyCull form of the cull test; kSplit: the default encoding (TC_FP16_SPLIT with G2L)
 // fixed at compile time, otherwise the encoding and frame come from p.
 template <bool kInspect, bool kStats, bool kQueue, bool kEarly, bool kSplit>
-__global__ void __launch_bounds__(kTcThreads) k_render_tc(TcParams p) {
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
@@ -824,8 +826,8 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return TCGS_ERR_CUDA;
     bool any_stats = false;
     for (int v = 0; v < n_views; ++v) any_stats = any_stats || views[v].tile_stats;
-    // persistent grid: at most the CTAs that are resident at once (3 per SM for this kernel)
-    int ctas = g_sm_count * 3;
+    // persistent grid: at most the CTAs that are resident at once (4 per SM for this kernel)
+    int ctas = g_sm_count * kTcCtasPerSm;
     if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
     if (ctas > n_items) ctas = n_items;
     return any_stats ? launch_tc<false, true, true>(p, ctas, s) : launch_tc<false, false, true>(p, ctas, s);
