@@ -247,32 +247,11 @@ __device__ __forceinline__ Cover cover_of(const float* __restrict__ mean2d, cons
     return v;
 }
 
-// Least value of the conic form over the tile's pixel-centre box [-h, h]^2 (tile-local mean lx, ly):
-// 0 when the mean is inside; otherwise on the edges facing the mean (a vertical one when the mean is
-// left or right of the box, a horizontal one when it is above or below), each minimised at its
-// clamped stationary point -- the same values min_q_box_r computes for those edges; the edges
-// facing away cannot hold the minimum of a convex form whose minimiser lies beyond the other side.
+// Gaussian v reaches the tile whose centre is at tile-local offset (lx, ly) from its mean when the
+// least value of its conic form over the tile's 16 x 16 pixel-centre box is within its reach limit.
 __device__ __forceinline__ bool tile_reached(const Cover& v, float lx, float ly) {
     constexpr float h = 0.5f * (kTile - 1);
-    if (!(v.lim >= 0.f)) return false;
-    const bool out_x = fabsf(lx) > h, out_y = fabsf(ly) > h;
-    if (!out_x && !out_y) return true;
-    float best = __int_as_float(0x7f800000);
-    if (out_x) {
-        const float X = lx > 0.f ? h : -h;
-        const float dx = lx - X;
-        const float y = fminf(h, fmaxf(-h, ly + v.b * dx * v.ic));
-        const float dy = ly - y;
-        best = fminf(best, v.a * dx * dx + 2.f * v.b * dx * dy + v.c * dy * dy);
-    }
-    if (out_y) {
-        const float Y = ly > 0.f ? h : -h;
-        const float ey = ly - Y;
-        const float x = fminf(h, fmaxf(-h, lx + v.b * ey * v.ia));
-        const float ex = lx - x;
-        best = fminf(best, v.a * ex * ex + 2.f * v.b * ex * ey + v.c * ey * ey);
-    }
-    return best <= v.lim;
+    return v.lim >= 0.f && min_q_box_facing(lx, ly, v.a, v.b, v.c, v.ia, v.ic, -h, h, -h, h) <= v.lim;
 }
 
 // Exact coverage, block-cooperative: the kThreads Gaussians of a block (thread t: Gaussian g_t) have

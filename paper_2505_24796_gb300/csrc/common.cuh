@@ -100,6 +100,31 @@ __device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float 
     return best;
 }
 
+// The same minimum from the edges facing m only: a vertical edge when m is left or right of the box,
+// a horizontal one when it is above or below (the edges facing away cannot hold the minimum of a
+// convex form whose minimiser lies beyond the opposite side); each is evaluated as above.
+__device__ __forceinline__ float min_q_box_facing(float mx, float my, float a, float b, float c, float ia, float ic,
+                                                  float x0, float x1, float y0, float y1) {
+    const bool lx = mx < x0, hx = mx > x1, ly = my < y0, hy = my > y1;
+    if (!(lx || hx || ly || hy)) return 0.f;
+    float best = __int_as_float(0x7f800000);
+    if (lx || hx) {
+        const float X = lx ? x0 : x1;
+        const float dx = mx - X;
+        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
+        const float dy = my - y;
+        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+    }
+    if (ly || hy) {
+        const float Y = ly ? y0 : y1;
+        const float ey = my - Y;
+        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
+        const float ex = mx - x;
+        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
+    }
+    return best;
+}
+
 // Reach limit of a Gaussian with ln-opacity lno: alpha = o exp(-q/2) >= 1/255 (Eq. 5) needs
 // q <= 2 (ln o + ln 255).  The relative and absolute margins keep every test built on it (the TC
 // renderer's block marks, the exact tile coverage of the sorting stage) conservative under FP32

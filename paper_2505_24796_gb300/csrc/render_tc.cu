@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
             const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + buf * kPBytes);
             const float4 a = sP[3 * lane], b = sP[3 * lane + 1];
             bool act = b.y >= 0.f;
-            if (act && p.tile_cull) act = min_q_box_r(a.x, a.y, a.z, a.w, b.x, b.z, b.w, bx0, bx1, by0, by1) <= b.y;
+            if (act && p.tile_cull) act = min_q_box_facing(a.x, a.y, a.z, a.w, b.x, b.z, b.w, bx0, bx1, by0, by1) <= b.y;
             return __ballot_sync(0xffffffffu, act);
         };
         // Producer lane 0: both 128-row halves of U against the same V, committed to one mbarrier.
