@@ -1,8 +1,8 @@
 """Benchmark of the TC-GS rasterizer hot path on one GB300 (or N replicas under torchrun).
 
 One step = one frame of the precision workload (1920x1080, fx = fy = 1100, 1M Gaussians in
-64 clusters, SH degree 3): project -> bin_sort -> render_fwd with the Frag2Mat tensor-core
-path (FP16 hi/lo split, G2L).  Inputs are resident in HBM; L2 is flushed between steps
+64 clusters, SH degree 3): project -> bin_sort (exact tile coverage) -> render_fwd with the
+Frag2Mat tensor-core path (FP16 hi/lo split, G2L).  Inputs are resident in HBM; L2 is flushed between steps
 (outside the timed events).  The same frame on the FP32 CUDA-core path is timed beside it.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the differentiation, scheduler and large workloads (reported beside the headline)")
     ap.add_argument("--sched-train-views", type=int, default=200)
-    ap.add_argument("--coverage", default="square", choices=["square", "exact"],
+    ap.add_argument("--coverage", default="exact", choices=["exact", "square"],
                     help="tile coverage of the headline binning: the 3-sigma square of the paper's pipeline, or "
                          "exact (tcgs_bin_sort_exact); the other one is timed beside it")
     return ap.parse_args()
@@ -232,8 +232,9 @@ def bench_differentiation(dev, flush):
     r.frame(d, precision="fp32")
     torch.cuda.synchronize()
     st = r.stats.to(torch.int64).sum(0).tolist()
+    n_exact = int(r.bins["n_splats"].item())
     r.stats = None
-    exact = _exact_coverage_render(cam, d, n + 1024, dev, flush)
+    square = _coverage_render(cam, d, n + 1024, dev, flush, exact=False)
     tgt = torch.from_numpy(target).to(dev)
     gimg = torch.sign(r.out["img"] - tgt).contiguous()
     P = len(sc["opacity"])
@@ -257,8 +258,8 @@ def bench_differentiation(dev, flush):
                                                      d["sh_degree"], r.proj["radius"], grads["dmean2d"],
                                                      grads["dconic"], grads["drgb"], grads=g3), 10, 3, flush)
     return {"workload": "differentiation: 1280x720, fx=fy=1280, 500k Gaussians (plain distributions), L1 to a "
-                        "seeded target; backward replays the FP32 forward", "splats": n,
-            "exact_coverage": exact,
+                        "seeded target; backward replays the FP32 forward; exact tile coverage",
+            "splats": n_exact, "square_coverage": square,
             "alpha_evals": st[0] + st[1], "f_blend": st[0],
             "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
                    "render_fwd_tc": fwdtc, "render_bwd": bwd_ms, "project_bwd": pbwd_ms},
@@ -342,8 +343,9 @@ def bench_large(dev, flush, steps=5, warmup=2):
     torch.cuda.synchronize()
     st = r.stats.to(torch.int64).sum(0).tolist()
     r.stats = None
-    out = {"workload": "large: 3840x2160, fx=fy=2200, 6M Gaussians (256 clusters, plain distributions), SH3",
-           "splats": n, "alpha_evals": st[0] + st[1]}
+    out = {"workload": "large: 3840x2160, fx=fy=2200, 6M Gaussians (256 clusters, plain distributions), SH3; "
+                       "exact tile coverage",
+           "splats": int(r.bins["n_splats"].item()), "alpha_evals": st[0] + st[1]}
     for prec in ("tc_fp16_split", "fp32"):
         stg = [_events_ms(lambda: r.project(d), steps, warmup, flush),
                _events_ms(lambda: r.bin_sort(), steps, warmup, flush),
@@ -363,15 +365,15 @@ def bench_large(dev, flush, steps=5, warmup=2):
         r.proj["rgb"], r.out["img"], r.out["T_final"], r.out["n_contrib"], gimg, grads=grads), 3, 1, flush)
     del r
     torch.cuda.empty_cache()
-    out["exact_coverage"] = _exact_coverage_render(cam, d, n + 1024, dev, flush, steps, warmup)
+    out["square_coverage"] = _coverage_render(cam, d, n + 1024, dev, flush, exact=False, steps=steps, warmup=warmup)
     return out
 
 
-def _exact_coverage_render(cam, d, capacity, dev, flush, steps=10, warmup=3):
-    """The same view binned with exact tile coverage: splats, bin_sort and both renderers' times."""
+def _coverage_render(cam, d, capacity, dev, flush, exact, steps=10, warmup=3):
+    """The same view binned with the given coverage rule: splats, bin_sort and both renderers' times."""
     import torch
     import paper_2505_24796_gb300 as tc
-    r = tc.Renderer(cam, d["means3"].shape[0], capacity, device=dev, exact_tiles=True)
+    r = tc.Renderer(cam, d["means3"].shape[0], capacity, device=dev, exact_tiles=exact)
     r.frame(d, precision="fp32")
     torch.cuda.synchronize()
     out = {"splats": int(r.bins["n_splats"].item()),
@@ -476,7 +478,7 @@ def bench_tight_radius(cam, sc, dsc, dev, flush, with_oracle=True, reps=20, warm
                          opacity=dsc["opacity"])
     n = int(pr["tiles_touched"].to(torch.int64).sum().item())
     del pr
-    r = tc.Renderer(cam, P, n + 1024, device=dev, tight_radius=True)
+    r = tc.Renderer(cam, P, n + 1024, device=dev, tight_radius=True, exact_tiles=False)
     tot, stg = time_frames(r, dsc, "tc_fp16_split", reps, warmup, True, flush, torch.cuda.current_stream(dev))
     ms = dict(zip(["project", "bin_sort", "render_fwd"], [statistics.mean(x) for x in stg]))
     r.frame(dsc, precision="tc_fp16_split")

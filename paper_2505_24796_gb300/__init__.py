@@ -349,10 +349,11 @@ class Renderer:
     project -> bin_sort -> render_fwd on the current stream with no host synchronisation."""
 
     def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False, tight_radius: bool = False,
-                 exact_tiles: bool = False):
+                 exact_tiles: bool = True):
         """tight_radius: bin with the opacity-aware coverage square instead of the 3-sigma one.
-        exact_tiles: keep only the tiles each Gaussian reaches with alpha >= 1/255
-        (tcgs_bin_sort_exact; the same images, shorter lists)."""
+        exact_tiles (default): keep only the tiles each Gaussian reaches with alpha >= 1/255
+        (tcgs_bin_sort_exact: the same images as the rectangle's tiles, shorter lists); False bins
+        every tile of the rectangle (tcgs_bin_sort)."""
         self.cam = _cam(cam)
         self.tight_radius = bool(tight_radius)
         self.exact_tiles = bool(exact_tiles)
@@ -521,7 +522,7 @@ class _Project(torch.autograd.Function):
 
 
 def render_gaussians(cam, means3, scales, quats, opacity, sh, sh_degree, precision="tc_fp16_split", alpha_max=0.99,
-                     bg=(0.0, 0.0, 0.0), tight_radius=False, capacity=None, exact_tiles=False):
+                     bg=(0.0, 0.0, 0.0), tight_radius=False, capacity=None, exact_tiles=True):
     """Differentiable frame from 3D Gaussians: project -> bin_sort -> render.  Gradients flow to
     means3, scales, quats, opacity and sh through tcgs_render_bwd and tcgs_project_bwd (binning is
     piecewise constant).  Returns (img [3,H,W], T_final [H,W]).  capacity None sizes the splat

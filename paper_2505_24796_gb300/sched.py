@@ -75,7 +75,7 @@ class MultiView:
             n = int(pr["tiles_touched"].to(torch.int64).sum().item())
             r = Renderer(cam, P, n + 1024, device=self.device, stats=True)
             r.proj = pr
-            r.bin_sort()
+            r.bin_sort(opacity=self.scene["opacity"])
             self.views.append(r)
         torch.cuda.synchronize(self.device)
 
