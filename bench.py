@@ -37,8 +37,8 @@ SM_COUNT, SM_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # workload, from the `ncu --set full` capture summarised in the named profile.  It is reported only
 # while the kernel's sources hash to the value they had when the counters were taken.
 NCU_TRAFFIC = {
-    "k_render_tc": {"bytes": 50167808 + 17995520,
-                    "sha256": "ab35a5e5d941fc7862294c19ea9aefb6823a9439e0874b85a21bfe8d4b13a76a",
+    "k_render_tc": {"bytes": 43769344 + 14565632,
+                    "sha256": "e663247e7002e3d7b89266c178fb2990de4c3eb653195d6ec4d3702b32422c02",
                     "sources": ["paper_2505_24796_gb300/csrc/render_tc.cu", "paper_2505_24796_gb300/csrc/common.cuh"],
                     "profile": "profiles/k_render_tc_precision_1920x1080.md"},
 }
