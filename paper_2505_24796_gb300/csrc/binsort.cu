@@ -254,6 +254,23 @@ __device__ __forceinline__ bool tile_reached(const Cover& v, float lx, float ly)
     return v.lim >= 0.f && min_q_box_facing(lx, ly, v.a, v.b, v.c, v.ia, v.ic, -h, h, -h, h) <= v.lim;
 }
 
+// Row and column of tile kk of a rectangle `w` tiles wide: the quotient from a float product and one
+// correction step (exact for kk < 2^22: the product is then within one of kk / w), integer division
+// beyond that.
+__device__ __forceinline__ void rect_row_col(uint32_t kk, uint32_t w, float inv_w, uint32_t& row, uint32_t& col) {
+    if (kk < (1u << 22)) {
+        uint32_t q = __float2uint_rz((float)kk * inv_w);
+        int32_t r = (int32_t)(kk - q * w);
+        if (r < 0) { --q; r += (int32_t)w; }
+        if (r >= (int32_t)w) { ++q; r -= (int32_t)w; }
+        row = q;
+        col = (uint32_t)r;
+    } else {
+        row = kk / w;
+        col = kk - row * w;
+    }
+}
+
 // Exact coverage, block-cooperative: the kThreads Gaussians of a block (thread t: Gaussian g_t) have
 // their rectangles' tiles dealt out over all threads, kThreads splats per round in Gaussian-major,
 // row-major order (so a Gaussian with thousands of tiles is spread over the whole block), and the
@@ -262,6 +279,7 @@ struct BlockCover {
     Cover cv[kThreads];
     uint4 rect[kThreads];        // x0, y0, width, exclusive prefix of the rectangle sizes
     uint32_t cnt[kThreads];      // rectangle sizes
+    float inv_w[kThreads];       // 1 / width
     uint32_t wsum[kWarps];
     uint32_t total;
 };
@@ -291,6 +309,7 @@ __device__ __forceinline__ uint32_t stage_block_cover(BlockCover& bc, const DevC
     if (COVER) bc.cv[t] = cv;
     bc.rect[t] = make_uint4(x0, y0, rw, pre);
     bc.cnt[t] = cnt;
+    bc.inv_w[t] = 1.f / (float)rw;
     if (t == 0) bc.total = total;
     __syncthreads();
     return cnt;
@@ -313,7 +332,9 @@ __device__ __forceinline__ void block_cover_splats(BlockCover& bc, uint32_t grid
             if (bc.rect[owner + step].w <= sidx) owner += step;
         const uint4 r = bc.rect[owner];
         const uint32_t kk = active ? sidx - r.w : 0u;
-        const uint32_t ty = r.y + kk / r.z, tx = r.x + kk % r.z;
+        uint32_t row, col;
+        rect_row_col(kk, r.z, bc.inv_w[owner], row, col);
+        const uint32_t ty = r.y + row, tx = r.x + col;
         const Cover& v = bc.cv[owner];
         const float lx = v.mx - (float)(tx * kTile + kTile / 2), ly = v.my - (float)(ty * kTile + kTile / 2);
         const bool pass = active && tile_reached(v, lx, ly);
@@ -479,7 +500,9 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
             if (s_bc.rect[owner + step].w <= sidx) owner += step;
         const uint4 r = s_bc.rect[owner];
         const uint32_t kk = sidx - r.w;
-        const uint32_t ty = r.y + kk / r.z, tx = r.x + kk % r.z;
+        uint32_t row, col;
+        rect_row_col(kk, r.z, s_bc.inv_w[owner], row, col);
+        const uint32_t ty = r.y + row, tx = r.x + col;
         tile_keys[first + sidx] = ty * (uint32_t)cam.grid_w + tx;
         vals[first + sidx] = s_g[owner];
     }

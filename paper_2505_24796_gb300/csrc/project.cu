@@ -1,8 +1,9 @@
 // project.cu -- preprocess stage (Sec. 3.1, Eq. 2): EWA projection of 3D Gaussians.
 //
 // One thread per Gaussian; the stage is HBM bound (read ~40 B + the SH coefficients,
-// write 44 B per Gaussian).  SH degree-3 coefficients (192 B per Gaussian) are read as
-// twelve 16-byte vectors.
+// write 44 B per Gaussian).  SH degree-3 coefficients (192 B per Gaussian) are staged per warp:
+// the warp's 32 rows (6 KB, contiguous) are loaded with coalesced 16-byte loads into shared memory,
+// then each thread reads its own row.
 #include "common.cuh"
 
 namespace tcgs {
@@ -38,14 +39,38 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     Y[15] = -kY33 * x * (xx - 3.f * yy);
 }
 
-__global__ void __launch_bounds__(256) k_project(DevCamera cam, int P, int deg, const float* __restrict__ means3,
-                                                 const float* __restrict__ scales, const float* __restrict__ quats,
-                                                 const float* __restrict__ sh, const float* __restrict__ opacity,
-                                                 float* __restrict__ mean2d,
-                                                 float* __restrict__ conic, float* __restrict__ depth,
-                                                 int32_t* __restrict__ radius, float* __restrict__ rgb,
-                                                 uint32_t* __restrict__ tiles_touched) {
+constexpr int kProjThreads = 128;
+constexpr int kShRow4 = 13;   // float4 slots per staged SH row: 12 used; the odd stride keeps a row's
+                              // 16-byte reads by 8 consecutive threads in distinct bank groups
+
+template <bool kStageSh>
+__global__ void __launch_bounds__(kProjThreads) k_project(DevCamera cam, int P, int deg,
+                                                          const float* __restrict__ means3,
+                                                          const float* __restrict__ scales,
+                                                          const float* __restrict__ quats,
+                                                          const float* __restrict__ sh,
+                                                          const float* __restrict__ opacity,
+                                                          float* __restrict__ mean2d,
+                                                          float* __restrict__ conic, float* __restrict__ depth,
+                                                          int32_t* __restrict__ radius, float* __restrict__ rgb,
+                                                          uint32_t* __restrict__ tiles_touched) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float4 s_sh[kStageSh ? kProjThreads / 32 : 1][kStageSh ? 32 * kShRow4 : 1];
+    if (kStageSh) {
+        // the warp's degree-3 rows, coalesced: float4 i of the warp's block goes to row i / 12
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int g0 = g - lane;
+        const int rows = P - g0 < 32 ? P - g0 : 32;
+        if (rows > 0) {
+            const float4* src = reinterpret_cast<const float4*>(sh) + (size_t)g0 * 12;
+#pragma unroll
+            for (int m = 0; m < 12; ++m) {
+                const int i = lane + 32 * m;
+                if (i < 12 * rows) s_sh[warp][(i / 12) * kShRow4 + i % 12] = src[i];
+            }
+        }
+        __syncwarp();
+    }
     if (g >= P) return;
     float m0 = means3[3 * g], m1 = means3[3 * g + 1], m2 = means3[3 * g + 2];
     // camera-space mean t = W mu
@@ -123,7 +148,8 @@ __global__ void __launch_bounds__(256) k_project(DevCamera cam, int P, int deg, 
                 float cr = 0.5f, cg = 0.5f, cb = 0.5f;
                 const float* s = sh + (size_t)g * K * 3;
                 if (deg == 3) {
-                    const float4* s4 = reinterpret_cast<const float4*>(s);
+                    const float4* s4 = kStageSh ? &s_sh[threadIdx.x >> 5][(threadIdx.x & 31) * kShRow4]
+                                                : reinterpret_cast<const float4*>(s);
                     float v[48];
 #pragma unroll
                     for (int i = 0; i < 12; ++i) {
@@ -361,10 +387,15 @@ extern "C" tcgs_status tcgs_project(const tcgs_camera* cam, int32_t P, int32_t s
         (sh_degree == 3 && (reinterpret_cast<uintptr_t>(sh) & 15)))
         return TCGS_ERR_INVALID;
     DevCamera dc = make_dev_camera(*cam);
-    int threads = 256;
-    int blocks = (P + threads - 1) / threads;
-    k_project<<<blocks, threads, 0, (cudaStream_t)stream>>>(dc, P, sh_degree, means3, scales, quats, sh, opacity, mean2d,
-                                                           conic, depth, radius, rgb, tiles_touched);
+    const int blocks = (P + kProjThreads - 1) / kProjThreads;
+    if (sh_degree == 3)
+        k_project<true><<<blocks, kProjThreads, 0, (cudaStream_t)stream>>>(dc, P, sh_degree, means3, scales, quats, sh,
+                                                                          opacity, mean2d, conic, depth, radius, rgb,
+                                                                          tiles_touched);
+    else
+        k_project<false><<<blocks, kProjThreads, 0, (cudaStream_t)stream>>>(dc, P, sh_degree, means3, scales, quats,
+                                                                           sh, opacity, mean2d, conic, depth, radius,
+                                                                           rgb, tiles_touched);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
