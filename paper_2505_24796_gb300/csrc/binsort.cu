@@ -315,13 +315,16 @@ __device__ __forceinline__ uint32_t stage_block_cover(BlockCover& bc, const DevC
     return cnt;
 }
 
-// Calls f(pass, sidx, owner, kk, tile, ex) for every splat of the block (every thread, every round;
-// pass false past the end), ex = the number of passing splats before this one in the block's order.
+// Calls f(pass, active, owner, tile, leader, cnt, rank) for every splat of the block, kThreads per
+// round (every thread, every round; active false past the end).  The lanes of a warp that hold
+// splats of the same Gaussian form a run of consecutive lanes: `leader` marks its first lane, `cnt`
+// is its number of passing splats and `rank` the number of them on lower lanes.  No barrier: the
+// warps of a round do not depend on one another.
 template <typename F>
 __device__ __forceinline__ void block_cover_splats(BlockCover& bc, uint32_t grid_w, F&& f) {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     const uint32_t total = bc.total;
-    uint32_t run = 0;
+    const uint32_t lt = (1u << lane) - 1u, le = (2u << lane) - 1u;   // lanes below / at or below
     for (uint32_t s0 = 0; s0 < total; s0 += kThreads) {
         const uint32_t sidx = s0 + (uint32_t)t;
         const bool active = sidx < total;
@@ -338,16 +341,23 @@ __device__ __forceinline__ void block_cover_splats(BlockCover& bc, uint32_t grid
         const Cover& v = bc.cv[owner];
         const float lx = v.mx - (float)(tx * kTile + kTile / 2), ly = v.my - (float)(ty * kTile + kTile / 2);
         const bool pass = active && tile_reached(v, lx, ly);
-        uint32_t round_total;
-        const uint32_t ex = block_exclusive_scan<uint32_t, kThreads>(pass ? 1u : 0u, bc.wsum, round_total);
-        f(pass, active, owner, kk, ty * grid_w + tx, run + ex);
-        run += round_total;
+        const int prev = __shfl_up_sync(0xffffffffu, owner, 1);
+        const bool leader = active && (lane == 0 || prev != owner);
+        const uint32_t leads = __ballot_sync(0xffffffffu, leader);
+        const uint32_t passes = __ballot_sync(0xffffffffu, pass);
+        const uint32_t at_or_below = leads & le;
+        const int first = at_or_below ? 31 - __clz(at_or_below) : 0;
+        const uint32_t above = leads & ~le;
+        const uint32_t end_mask = above ? (1u << (__ffs(above) - 1)) - 1u : 0xFFFFFFFFu;
+        const uint32_t run = end_mask & ~((1u << first) - 1u);
+        f(pass, active, owner, ty * grid_w + tx, leader, (uint32_t)__popc(passes & run),
+          (uint32_t)__popc(passes & run & lt), first);
     }
 }
 
 // Depth keys, per-Gaussian splat counts, range clearing and the digit totals of pass 0.  The count
 // is the rectangle's tile count, or with EXACT the number of its tiles that pass the coverage test
-// (the difference of the block's running pass count at the Gaussian's first and last splat).
+// (added up per Gaussian in shared memory, one atomic per warp run).
 template <bool EXACT>
 __global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, const float* __restrict__ mean2d,
                                                        const int32_t* __restrict__ radius,
@@ -371,17 +381,17 @@ __global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, con
         return;
     }
     __shared__ BlockCover s_bc;
-    __shared__ uint32_t s_first[kThreads], s_last[kThreads];
+    __shared__ uint32_t s_cnt[kThreads];
     if ((int)(blockIdx.x * blockDim.x) >= P) return;   // the whole block is past the end
-    const uint32_t cnt = stage_block_cover(s_bc, cam, i < P, (uint32_t)i, mean2d, radius, conic, opacity);
-    block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool active, int owner, uint32_t kk, uint32_t,
-                                                      uint32_t before) {
-        if (active && kk == 0) s_first[owner] = before;
-        if (active && kk + 1 == s_bc.cnt[owner]) s_last[owner] = before + (pass ? 1u : 0u);
+    s_cnt[threadIdx.x] = 0u;
+    stage_block_cover(s_bc, cam, i < P, (uint32_t)i, mean2d, radius, conic, opacity);   // ends with a barrier
+    block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool, bool, int owner, uint32_t, bool leader, uint32_t cnt,
+                                                      uint32_t, int) {
+        if (leader && cnt) atomicAdd(&s_cnt[owner], cnt);
     });
     __syncthreads();
     if (i < P) {
-        const uint32_t c = cnt ? s_last[threadIdx.x] - s_first[threadIdx.x] : 0u;
+        const uint32_t c = s_cnt[threadIdx.x];
         counts[i] = c;
         keys[i] = c ? orderable_bits(depth[i]) : 0xFFFFFFFFu;
         vals[i] = (uint32_t)i;
@@ -459,6 +469,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
                                                         const uint32_t* __restrict__ n_u32) {
     __shared__ BlockCover s_bc;
     __shared__ uint32_t s_g[kThreads];
+    __shared__ uint32_t s_off[kThreads], s_used[kThreads];
     __shared__ uint32_t s_first;
     const uint32_t n_total = *n_u32;
     if (n_total == 0u || blockIdx.x * blockDim.x >= P) return;   // nothing to place, or past the end
@@ -475,12 +486,18 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
     if (threadIdx.x == 0) s_first = off;
     s_g[threadIdx.x] = g;
     if (EXACT) {
-        // each round's passing splats are packed by a block scan
-        stage_block_cover(s_bc, cam, listed, g, mean2d, radius, conic, opacity);
-        const uint32_t first = s_first;
-        block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool, int owner, uint32_t, uint32_t tile,
-                                                          uint32_t before) {
-            const uint32_t pos = first + before;
+        // a Gaussian's passing tiles fill its own range [offset, offset + count) in any order (the
+        // stable tile passes keep only the order between Gaussians); each warp run claims a slice
+        // of it with one shared-memory atomic
+        s_off[threadIdx.x] = off;
+        s_used[threadIdx.x] = 0u;
+        stage_block_cover(s_bc, cam, listed, g, mean2d, radius, conic, opacity);   // ends with a barrier
+        block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool, int owner, uint32_t tile, bool leader,
+                                                          uint32_t cnt, uint32_t rank, int first) {
+            uint32_t base = 0;
+            if (leader && cnt) base = atomicAdd(&s_used[owner], cnt);
+            base = __shfl_sync(0xffffffffu, base, first);
+            const uint32_t pos = s_off[owner] + base + rank;
             if (pass && pos < n_total) {   // always below N: the counts came from the same test
                 tile_keys[pos] = tile;
                 vals[pos] = s_g[owner];
