@@ -100,6 +100,12 @@ typedef struct {
                                 its pixels terminated, [5] the tile's CTA time in SM clock cycles / 64,
                                 [6], [7] reserved (0) */
     int32_t* device_status;  /* nullable device int32: set to a tcgs_status on a device-side error */
+    const uint32_t* tile_order; /* nullable device [num_tiles]: TC precisions in tile-local coordinates
+                                render with a persistent grid (4 CTAs per SM) that takes the tiles in this
+                                order, a permutation of all tiles such as tcgs_tile_order's (the order
+                                changes the schedule, never the image); NULL: one CTA per tile */
+    uint32_t* work_counter;  /* device uint32, required with tile_order: the grid's next-tile counter,
+                                zeroed by the call */
 } tcgs_render_opts;
 
 /* Human-readable name of a status code (static string). */
@@ -250,6 +256,16 @@ TCGS_API tcgs_status tcgs_render_fwd(const tcgs_camera* cam /* host */, const tc
                             const float* conic, const float* opacity, const float* rgb,
                             const float* bg3 /* host */, float* img, float* T_final, uint32_t* n_contrib,
                             tcgs_stream stream);
+
+/*
+ * Longest-first order of a view's tiles for the persistent renderer (tcgs_render_opts.tile_order):
+ * every tile once, grouped by floor(log2(list length)) from the longest group to the empty tiles;
+ * the order inside a group is unspecified (it decides only which CTA renders a tile, and when).  The
+ * paper has no counterpart: its blending launches one thread block per tile.
+ * In:  tile_ranges [num_tiles, 2] from the sorting stage.  Out: tile_order [num_tiles] (device).
+ */
+TCGS_API tcgs_status tcgs_tile_order(const tcgs_camera* cam /* host */, const uint32_t* tile_ranges,
+                                     uint32_t* tile_order, tcgs_stream stream);
 
 /* Largest number of views one batched launch can render. */
 #define TCGS_MAX_VIEWS 16

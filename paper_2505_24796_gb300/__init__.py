@@ -25,7 +25,7 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_GLOBAL, TCG
 TILE = 16
 
 __all__ = ["tcgs_project", "tcgs_project_bwd", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
-           "tcgs_bin_sort_exact",
+           "tcgs_bin_sort_exact", "tcgs_tile_order",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
            "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS", "FramePipeline",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
@@ -77,9 +77,10 @@ def _cam(cam) -> tcgs_camera:
 
 
 def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=None, tile_stats=None,
-                device_status=None, tile_cull=True) -> tcgs_render_opts:
+                device_status=None, tile_cull=True, tile_order=None, work_counter=None) -> tcgs_render_opts:
     """early_cull None: the path's default (off on the FP32 path, the 3DGS baseline; on for the
-    tensor-core paths, as the paper's renderer)."""
+    tensor-core paths, as the paper's renderer).  tile_order / work_counter: the persistent TC
+    renderer's tile order (tcgs_tile_order) and its counter."""
     o = tcgs_render_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.alpha_max = float(alpha_max)
@@ -87,6 +88,8 @@ def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=None, tile
     o.tile_cull = int(bool(tile_cull))
     o.tile_stats = _ptr(tile_stats, torch.int32, "tile_stats") if tile_stats is not None else None
     o.device_status = _ptr(device_status, torch.int32, "device_status") if device_status is not None else None
+    o.tile_order = _ptr(tile_order, torch.int32, "tile_order") if tile_order is not None else None
+    o.work_counter = _ptr(work_counter, torch.int32, "work_counter") if work_counter is not None else None
     return o
 
 
@@ -166,6 +169,17 @@ def tcgs_bin_sort_exact(cam, mean2d, radius, depth, conic, opacity, capacity: in
                         stream=None) -> dict:
     """tcgs_bin_sort_exact: splats only for the tiles each Gaussian reaches with alpha >= 1/255."""
     return tcgs_bin_sort(cam, mean2d, radius, depth, capacity, workspace, out, stream, conic=conic, opacity=opacity)
+
+
+def tcgs_tile_order(cam, tile_ranges, out=None, stream=None) -> torch.Tensor:
+    """Longest-first order of the view's tiles for the persistent renderer."""
+    c = _cam(cam)
+    nt = grid(c)[0] * grid(c)[1]
+    if out is None:
+        out = torch.empty(nt, dtype=torch.int32, device=tile_ranges.device)
+    check("tcgs_tile_order", _L().tcgs_tile_order(ctypes.byref(c), _ptr(tile_ranges, torch.int32, "tile_ranges"),
+                                                  _ptr(out, torch.int32, "tile_order"), _stream(stream)))
+    return out
 
 
 def tcgs_bin_sort_noalloc(cam, mean2d, radius, depth, capacity: int, out=None, stream=None) -> dict:
@@ -344,16 +358,21 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
     return out
 
 
+_PERSISTENT_PRECISIONS = ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8")
+
+
 class Renderer:
     """Preallocated buffers for one camera, scene size and splat capacity; ``frame`` runs
     project -> bin_sort -> render_fwd on the current stream with no host synchronisation."""
 
     def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False, tight_radius: bool = False,
-                 exact_tiles: bool = True):
+                 exact_tiles: bool = True, persistent: bool = True):
         """tight_radius: bin with the opacity-aware coverage square instead of the 3-sigma one.
         exact_tiles (default): keep only the tiles each Gaussian reaches with alpha >= 1/255
         (tcgs_bin_sort_exact: the same images as the rectangle's tiles, shorter lists); False bins
-        every tile of the rectangle (tcgs_bin_sort)."""
+        every tile of the rectangle (tcgs_bin_sort).  persistent (default): the tensor-core renders
+        take the tiles longest list first on a persistent grid (tcgs_tile_order); the image is the
+        same as with one CTA per tile."""
         self.cam = _cam(cam)
         self.tight_radius = bool(tight_radius)
         self.exact_tiles = bool(exact_tiles)
@@ -377,6 +396,9 @@ class Renderer:
         self.stats = (torch.zeros(self.num_tiles, _lib.TILE_STATS_WORDS, dtype=torch.int32, device=dev)
                       if stats else None)
         self.device_status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.persistent = bool(persistent)
+        self.tile_order = torch.empty(self.num_tiles, dtype=torch.int32, device=dev)
+        self.work_counter = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def project(self, scene: dict, stream=None):
         self.opacity = scene["opacity"]
@@ -396,7 +418,11 @@ class Renderer:
 
     def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=None, bg=(0, 0, 0),
                stream=None, tile_cull=True):
-        opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status, tile_cull)
+        order = None
+        if self.persistent and precision in _PERSISTENT_PRECISIONS:
+            order = tcgs_tile_order(self.cam, self.bins["tile_ranges"], out=self.tile_order, stream=stream)
+        opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status, tile_cull,
+                           tile_order=order, work_counter=self.work_counter if order is not None else None)
         return tcgs_render_fwd(self.cam, opts, self.bins["tile_ranges"], self.bins["ids_sorted"],
                                self.proj["mean2d"], self.proj["conic"], opacity, self.proj["rgb"], bg=bg,
                                out=self.out, stream=stream)

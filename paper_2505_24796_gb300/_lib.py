@@ -31,7 +31,8 @@ class tcgs_camera(ctypes.Structure):
 
 class tcgs_render_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("alpha_max", c_float), ("early_cull", c_int32), ("tile_cull", c_int32),
-                ("tile_stats", c_void_p), ("device_status", c_void_p)]
+                ("tile_stats", c_void_p), ("device_status", c_void_p), ("tile_order", c_void_p),
+                ("work_counter", c_void_p)]
 
 
 TCGS_MAX_VIEWS = 16
@@ -59,6 +60,7 @@ SIGNATURES = {
     "tcgs_bin_sort": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
     "tcgs_bin_sort_noalloc": (c_int32, [P_CAM, c_int32, V, V, V, c_int64, V, V, V, V, V]),
     "tcgs_bin_sort_exact": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int64, V, c_size_t, V, V, V, V, V]),
+    "tcgs_tile_order": (c_int32, [P_CAM, V, V, V]),
     "tcgs_render_fwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_render_bwd": (c_int32, [P_CAM, P_OPT, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V, V]),
     "tcgs_render_fwd_batched": (c_int32, [c_int32, V, P_OPT, V, V, V, c_int32, V, c_int32, V]),

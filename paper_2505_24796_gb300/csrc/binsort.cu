@@ -753,6 +753,54 @@ extern "C" tcgs_status tcgs_bin_sort_exact(const tcgs_camera* cam, int32_t P, co
                           ids_sorted, tile_ranges, n_splats, status, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------- longest-first tile order
+
+namespace tcgs {
+namespace {
+
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderGroups = 33;   // floor(log2(length)) + 1 for lengths 1 .. 2^32 - 1, and 0 for empty
+
+__device__ __forceinline__ int length_group(uint32_t len) { return len ? 32 - __clz(len) : 0; }
+
+// One CTA: counts the tiles of each length group, lays the groups out from the longest to the empty
+// one, and places every tile with a shared-memory cursor of its group.
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t* __restrict__ ranges, uint32_t T,
+                                                             uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[kOrderGroups], cursor[kOrderGroups];
+    const int t = threadIdx.x;
+    if (t < kOrderGroups) cnt[t] = 0u;
+    __syncthreads();
+    for (uint32_t i = t; i < T; i += kOrderThreads) atomicAdd(&cnt[length_group(ranges[2 * i + 1] - ranges[2 * i])], 1u);
+    __syncthreads();
+    if (t == 0) {
+        uint32_t run = 0;
+        for (int g = kOrderGroups - 1; g >= 0; --g) {
+            cursor[g] = run;
+            run += cnt[g];
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = t; i < T; i += kOrderThreads)
+        order[atomicAdd(&cursor[length_group(ranges[2 * i + 1] - ranges[2 * i])], 1u)] = i;
+}
+
+}  // namespace
+}  // namespace tcgs
+
+extern "C" tcgs_status tcgs_tile_order(const tcgs_camera* cam, const uint32_t* tile_ranges, uint32_t* tile_order,
+                                       tcgs_stream stream) {
+    using namespace tcgs;
+    if (!valid_camera(cam) || !tile_ranges || !tile_order) return TCGS_ERR_INVALID;
+    const DevCamera dc = make_dev_camera(*cam);
+    const uint64_t T = (uint64_t)dc.grid_w * dc.grid_h;
+    if (T > 0xFFFFFFFFull) return TCGS_ERR_INVALID;
+    k_tile_order<<<1, kOrderThreads, 0, (cudaStream_t)stream>>>(tile_ranges, (uint32_t)T, tile_order);
+    count_launches(1);
+    TCGS_CHECK_LAUNCH();
+    return TCGS_OK;
+}
+
 // ---------------------------------------------------------------- work-queue ordering
 
 namespace tcgs {

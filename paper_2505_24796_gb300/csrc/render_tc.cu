@@ -242,6 +242,7 @@ struct TcParams {
     int32_t* status;
     int n_views;
     const uint32_t* queue;      // queue mode: items (view << 16 | tile) in the order to render
+    int queue_tiles;            // queue mode, one view: the items are plain tile indices
     uint32_t n_items;
     uint32_t* counter;          // queue mode: next item to take (zeroed before the launch)
     const int32_t* dbg_tiles;   // frag2mat inspection mode
@@ -345,8 +346,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
             const uint32_t item = s_item;
             if (item >= p.n_items) break;
             const uint32_t it = p.queue[item];
-            view = (int)(it >> 16);
-            tile = (int)(it & 0xFFFFu);
+            view = p.queue_tiles ? 0 : (int)(it >> 16);
+            tile = p.queue_tiles ? (int)it : (int)(it & 0xFFFFu);
         } else {
             if (round > 0) break;
             tile = kInspect ? p.dbg_tiles[blockIdx.x] : (int)blockIdx.x;
@@ -750,6 +751,19 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
     p.tile_cull = p.global ? 0 : opts->tile_cull;   // the ablation walks every entry
     p.early_cull = opts->early_cull;
     const int tiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
+    if (opts->tile_order && !p.global) {
+        // persistent grid over the tiles in the given order: each CTA allocates TMEM and builds U
+        // once, and the longest lists start first
+        if (!opts->work_counter) return TCGS_ERR_INVALID;
+        p.queue = opts->tile_order;
+        p.queue_tiles = 1;
+        p.n_items = (uint32_t)tiles;
+        p.counter = opts->work_counter;
+        if (cudaMemsetAsync(opts->work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return TCGS_ERR_CUDA;
+        int ctas = g_sm_count * kTcCtasPerSm;
+        if (ctas > tiles) ctas = tiles;
+        return opts->tile_stats ? launch_tc<false, true, true>(p, ctas, s) : launch_tc<false, false, true>(p, ctas, s);
+    }
     return opts->tile_stats ? launch_tc<false, true, false>(p, tiles, s) : launch_tc<false, false, false>(p, tiles, s);
 }
 

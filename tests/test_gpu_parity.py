@@ -324,6 +324,36 @@ def test_frame_pipeline_matches_direct_frames(tc):
     assert not torch.equal(host[0], host[1])
 
 
+@pytest.mark.parametrize("name,make", SMALL[1:])
+def test_persistent_render_matches_one_cta_per_tile(tc, name, make):
+    """The persistent TC renderer (tiles taken longest list first, tcgs_tile_order) gives the image,
+    T and n_contrib of one CTA per tile bit for bit, for every tile-local encoding; its order is a
+    permutation of the tiles with non-increasing list-length groups."""
+    cam, sc = make()
+    dsc = {k: to_torch(v, DEV) if isinstance(v, np.ndarray) else v for k, v in sc.items()}
+    P = len(sc["opacity"])
+    cap = int(oracle.project(cam, scene64(sc))["tiles_touched"].sum()) + 64
+    outs = {}
+    for persistent in (False, True):
+        r = tc.Renderer(cam, P, cap, device=DEV, persistent=persistent)
+        r.project(dsc)
+        r.bin_sort()
+        for prec in ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8"):
+            o = r.render(dsc["opacity"], prec)
+            torch.cuda.synchronize()
+            outs[(persistent, prec)] = {k: v.clone() for k, v in o.items()}
+        if persistent:
+            order = r.tile_order.cpu().numpy()
+            lens = np.diff(r.bins["tile_ranges"].cpu().numpy(), axis=1).ravel().astype(np.int64)
+    for prec in ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8"):
+        a, b = outs[(False, prec)], outs[(True, prec)]
+        for k in ("img", "T_final", "n_contrib"):
+            assert torch.equal(a[k], b[k]), (prec, k)
+    np.testing.assert_array_equal(np.sort(order), np.arange(len(lens)))
+    groups = np.where(lens[order] > 0, np.floor(np.log2(np.maximum(lens[order], 1))) + 1, 0)
+    assert (np.diff(groups) <= 0).all()
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
