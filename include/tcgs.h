@@ -259,9 +259,10 @@ TCGS_API tcgs_status tcgs_render_fwd(const tcgs_camera* cam /* host */, const tc
 
 /*
  * Longest-first order of a view's tiles for the persistent renderer (tcgs_render_opts.tile_order):
- * every tile once, grouped by floor(log2(list length)) from the longest group to the empty tiles;
- * the order inside a group is unspecified (it decides only which CTA renders a tile, and when).  The
- * paper has no counterpart: its blending launches one thread block per tile.
+ * every tile once, grouped by floor(log2(list length)) from the longest group to the empty tiles,
+ * in tile order inside a group (neighbouring tiles share Gaussians).  The order decides only which
+ * CTA renders a tile, and when.  The paper has no counterpart: its blending launches one thread
+ * block per tile.
  * In:  tile_ranges [num_tiles, 2] from the sorting stage.  Out: tile_order [num_tiles] (device).
  */
 TCGS_API tcgs_status tcgs_tile_order(const tcgs_camera* cam /* host */, const uint32_t* tile_ranges,

@@ -764,11 +764,15 @@ constexpr int kOrderGroups = 33;   // floor(log2(length)) + 1 for lengths 1 .. 2
 __device__ __forceinline__ int length_group(uint32_t len) { return len ? 32 - __clz(len) : 0; }
 
 // One CTA: counts the tiles of each length group, lays the groups out from the longest to the empty
-// one, and places every tile with a shared-memory cursor of its group.
+// one, and places the tiles of a group in tile order (a stable counting sort: chunks of 1024 tiles in
+// order, ranked inside a warp by __match_any_sync and across the warps of a chunk by their counts), so
+// that tiles close on screen, which share Gaussians, stay close in the schedule.
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t* __restrict__ ranges, uint32_t T,
                                                              uint32_t* __restrict__ order) {
+    constexpr int NW = kOrderThreads / 32;
     __shared__ uint32_t cnt[kOrderGroups], cursor[kOrderGroups];
-    const int t = threadIdx.x;
+    __shared__ uint32_t wcnt[NW][kOrderGroups];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t < kOrderGroups) cnt[t] = 0u;
     __syncthreads();
     for (uint32_t i = t; i < T; i += kOrderThreads) atomicAdd(&cnt[length_group(ranges[2 * i + 1] - ranges[2 * i])], 1u);
@@ -780,9 +784,29 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t* __
             run += cnt[g];
         }
     }
-    __syncthreads();
-    for (uint32_t i = t; i < T; i += kOrderThreads)
-        order[atomicAdd(&cursor[length_group(ranges[2 * i + 1] - ranges[2 * i])], 1u)] = i;
+    for (uint32_t c0 = 0; c0 < T; c0 += kOrderThreads) {
+        const uint32_t i = c0 + t;
+        const bool valid = i < T;
+        const int g = valid ? length_group(ranges[2 * i + 1] - ranges[2 * i]) : kOrderGroups + lane;
+        for (int k = t; k < NW * kOrderGroups; k += kOrderThreads) (&wcnt[0][0])[k] = 0u;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, g);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][g] = __popc(peers);
+        __syncthreads();
+        if (t < kOrderGroups) {   // exclusive prefix over the warps, per group, after the group's cursor
+            uint32_t run = cursor[t];
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t c = wcnt[w][t];
+                wcnt[w][t] = run;
+                run += c;
+            }
+            cursor[t] = run;
+        }
+        __syncthreads();
+        if (valid) order[wcnt[warp][g] + rank] = i;
+        __syncthreads();
+    }
 }
 
 }  // namespace

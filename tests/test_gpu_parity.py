@@ -352,6 +352,8 @@ def test_persistent_render_matches_one_cta_per_tile(tc, name, make):
     np.testing.assert_array_equal(np.sort(order), np.arange(len(lens)))
     groups = np.where(lens[order] > 0, np.floor(np.log2(np.maximum(lens[order], 1))) + 1, 0)
     assert (np.diff(groups) <= 0).all()
+    same = np.diff(groups) == 0
+    assert (np.diff(order)[same] > 0).all()   # tile order inside a group
 
 
 # ------------------------------------------------------------------ alpha blending
