@@ -147,12 +147,22 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Gradient partial sums of a fragment: each warp reduces its 32 pixels' contributions with shuffles
+// and parks the 9 sums in shared memory; every kBwdChunk fragments the block adds the 8 warps' sums
+// and issues one global atomic per (fragment, parameter) -- 8 times fewer same-address atomics than
+// one per warp.
+constexpr int kBwdChunk = 32;
+constexpr int kBwdWarps = kFwdThreads / 32;
+constexpr int kBwdParams = 9;   // dmean2d (2), dconic (3), dopacity, drgb (3)
+
 __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
     __shared__ float2 s_xy[kFwdThreads];
     __shared__ float4 s_co[kFwdThreads];
     __shared__ float4 s_rgb[kFwdThreads];
     __shared__ uint32_t s_id[kFwdThreads];
     __shared__ uint32_t s_max;
+    __shared__ float s_part[kBwdChunk][kBwdWarps][kBwdParams];
+    const int warp = threadIdx.x >> 5;
     const int tile = blockIdx.x;
     const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
     const int t = threadIdx.x, lane = t & 31;
@@ -226,20 +236,37 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
                     T = fmaf(-alpha, T, T);
                 }
             }
+            float* part = s_part[j % kBwdChunk][warp];
             if (__any_sync(0xffffffffu, contrib)) {
                 dm0 = warp_sum(dm0); dm1 = warp_sum(dm1);
                 dc0 = warp_sum(dc0); dc1 = warp_sum(dc1); dc2 = warp_sum(dc2);
                 dop = warp_sum(dop);
                 dr0 = warp_sum(dr0); dr1 = warp_sum(dr1); dr2 = warp_sum(dr2);
                 if (lane == 0) {
-                    uint32_t g = s_id[j];
-                    atomicAdd(&p.dmean2d[2 * g], dm0); atomicAdd(&p.dmean2d[2 * g + 1], dm1);
-                    atomicAdd(&p.dconic[3 * g], dc0); atomicAdd(&p.dconic[3 * g + 1], dc1);
-                    atomicAdd(&p.dconic[3 * g + 2], dc2);
-                    atomicAdd(&p.dopacity[g], dop);
-                    atomicAdd(&p.drgb[3 * g], dr0); atomicAdd(&p.drgb[3 * g + 1], dr1);
-                    atomicAdd(&p.drgb[3 * g + 2], dr2);
+                    part[0] = dm0; part[1] = dm1; part[2] = dc0; part[3] = dc1; part[4] = dc2;
+                    part[5] = dop; part[6] = dr0; part[7] = dr1; part[8] = dr2;
                 }
+            } else if (lane < kBwdParams) {
+                part[lane] = 0.f;
+            }
+            if ((j + 1) % kBwdChunk == 0 || j + 1 == nb) {
+                // the block adds the warps' sums of the chunk's fragments: one atomic per value
+                __syncthreads();
+                const uint32_t j0 = j - j % kBwdChunk, nf = j + 1 - j0;
+                for (uint32_t q = threadIdx.x; q < nf * kBwdParams; q += kFwdThreads) {
+                    const uint32_t f = q / kBwdParams, k = q - f * kBwdParams;
+                    float v = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kBwdWarps; ++w) v += s_part[f][w][k];
+                    if (v != 0.f) {
+                        const uint32_t g = s_id[j0 + f];
+                        float* dst = k < 2 ? &p.dmean2d[2 * g + k]
+                                           : (k < 5 ? &p.dconic[3 * g + (k - 2)]
+                                                    : (k == 5 ? &p.dopacity[g] : &p.drgb[3 * g + (k - 6)]));
+                        atomicAdd(dst, v);
+                    }
+                }
+                __syncthreads();
             }
         }
     }
