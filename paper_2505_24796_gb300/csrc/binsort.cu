@@ -278,7 +278,6 @@ __device__ __forceinline__ void rect_row_col(uint32_t kk, uint32_t w, float inv_
 struct BlockCover {
     Cover cv[kThreads];
     uint4 rect[kThreads];        // x0, y0, width, exclusive prefix of the rectangle sizes
-    uint32_t cnt[kThreads];      // rectangle sizes
     float inv_w[kThreads];       // 1 / width
     uint32_t wsum[kWarps];
     uint32_t total;
@@ -308,7 +307,6 @@ __device__ __forceinline__ uint32_t stage_block_cover(BlockCover& bc, const DevC
     const uint32_t pre = block_exclusive_scan<uint32_t, kThreads>(cnt, bc.wsum, total);
     if (COVER) bc.cv[t] = cv;
     bc.rect[t] = make_uint4(x0, y0, rw, pre);
-    bc.cnt[t] = cnt;
     bc.inv_w[t] = 1.f / (float)rw;
     if (t == 0) bc.total = total;
     __syncthreads();

@@ -78,31 +78,10 @@ __device__ __forceinline__ uint32_t rect_count(const Rect& r) {
 
 // Smallest value of q(p) = (m - p)^T Q (m - p) over the rectangle [x0, x1] x [y0, y1] of pixel
 // centres, Q = [[a, b], [b, c]] positive definite, with ia = 1/a and ic = 1/c precomputed: 0 when m
-// is inside, otherwise the smallest of the four edge minima (each a 1-D convex quadratic minimised
-// at its clamped stationary point).
-__device__ __forceinline__ float min_q_box_r(float mx, float my, float a, float b, float c, float ia, float ic,
-                                             float x0, float x1, float y0, float y1) {
-    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.f;
-    float best = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float X = e ? x1 : x0;
-        const float dx = mx - X;
-        const float y = fminf(y1, fmaxf(y0, my + b * dx * ic));
-        const float dy = my - y;
-        best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
-        const float Y = e ? y1 : y0;
-        const float ey = my - Y;
-        const float x = fminf(x1, fmaxf(x0, mx + b * ey * ia));
-        const float ex = mx - x;
-        best = fminf(best, a * ex * ex + 2.f * b * ex * ey + c * ey * ey);
-    }
-    return best;
-}
-
-// The same minimum from the edges facing m only: a vertical edge when m is left or right of the box,
-// a horizontal one when it is above or below (the edges facing away cannot hold the minimum of a
-// convex form whose minimiser lies beyond the opposite side); each is evaluated as above.
+// is inside; otherwise it lies on an edge facing m -- a vertical edge when m is left or right of the
+// rectangle, a horizontal one when m is above or below (the edges facing away cannot hold the
+// minimum of a convex form whose minimiser lies beyond the opposite side) -- where the form is a 1-D
+// convex quadratic minimised at its clamped stationary point.
 __device__ __forceinline__ float min_q_box_facing(float mx, float my, float a, float b, float c, float ia, float ic,
                                                   float x0, float x1, float y0, float y1) {
     const bool lx = mx < x0, hx = mx > x1, ly = my < y0, hy = my > y1;
