@@ -37,8 +37,8 @@ SM_COUNT, SM_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # workload, from the `ncu --set full` capture summarised in the named profile.  It is reported only
 # while the kernel's sources hash to the value they had when the counters were taken.
 NCU_TRAFFIC = {
-    "k_render_tc": {"bytes": 43769344 + 14565632,
-                    "sha256": "e663247e7002e3d7b89266c178fb2990de4c3eb653195d6ec4d3702b32422c02",
+    "k_render_tc": {"bytes": 43568128 + 9463808,
+                    "sha256": "afc26ff271a0e0a8c0cce5a32a5379ab3670edba071feb6d47fa2d1b7141f447",
                     "sources": ["paper_2505_24796_gb300/csrc/render_tc.cu", "paper_2505_24796_gb300/csrc/common.cuh"],
                     "profile": "profiles/k_render_tc_precision_1920x1080.md"},
 }

@@ -761,49 +761,80 @@ constexpr int kOrderGroups = 33;   // floor(log2(length)) + 1 for lengths 1 .. 2
 
 __device__ __forceinline__ int length_group(uint32_t len) { return len ? 32 - __clz(len) : 0; }
 
-// One CTA: counts the tiles of each length group, lays the groups out from the longest to the empty
-// one, and places the tiles of a group in tile order (a stable counting sort: chunks of 1024 tiles in
-// order, ranked inside a warp by __match_any_sync and across the warps of a chunk by their counts), so
-// that tiles close on screen, which share Gaussians, stay close in the schedule.
+// One CTA, a stable counting sort: the groups are laid out from the longest to the empty one, and the
+// tiles of a group stay in tile order, so that tiles close on screen, which share Gaussians, stay
+// close in the schedule.  Each warp owns a contiguous run of tiles: it counts its run's tiles per
+// group, the block turns those counts into the start of every (group, warp) segment, and the warp
+// places its tiles in order, ranked among 32 consecutive tiles by __match_any_sync.  The groups of
+// the first kOrderCache tiles are read from global memory once, into shared memory.
+constexpr int kOrderCache = 32768;
+static_assert(kOrderGroups == 33 && kOrderThreads == 1024, "the scans below take 32 warps and 33 groups");
+
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t* __restrict__ ranges, uint32_t T,
                                                              uint32_t* __restrict__ order) {
     constexpr int NW = kOrderThreads / 32;
-    __shared__ uint32_t cnt[kOrderGroups], cursor[kOrderGroups];
-    __shared__ uint32_t wcnt[NW][kOrderGroups];
+    __shared__ uint8_t s_g[kOrderCache];
+    __shared__ uint32_t s_cur[NW][kOrderGroups];   // this warp's tiles of a group, then its next slot there
+    __shared__ uint32_t s_base[kOrderGroups];      // a group's total, then its first slot
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    if (t < kOrderGroups) cnt[t] = 0u;
+    const uint32_t cached = T < (uint32_t)kOrderCache ? T : (uint32_t)kOrderCache;
+    for (uint32_t i = t; i < cached; i += kOrderThreads)
+        s_g[i] = (uint8_t)length_group(ranges[2 * i + 1] - ranges[2 * i]);
+    for (int k = t; k < NW * kOrderGroups; k += kOrderThreads) (&s_cur[0][0])[k] = 0u;
     __syncthreads();
-    for (uint32_t i = t; i < T; i += kOrderThreads) atomicAdd(&cnt[length_group(ranges[2 * i + 1] - ranges[2 * i])], 1u);
-    __syncthreads();
-    if (t == 0) {
-        uint32_t run = 0;
-        for (int g = kOrderGroups - 1; g >= 0; --g) {
-            cursor[g] = run;
-            run += cnt[g];
-        }
-    }
-    for (uint32_t c0 = 0; c0 < T; c0 += kOrderThreads) {
-        const uint32_t i = c0 + t;
-        const bool valid = i < T;
-        const int g = valid ? length_group(ranges[2 * i + 1] - ranges[2 * i]) : kOrderGroups + lane;
-        for (int k = t; k < NW * kOrderGroups; k += kOrderThreads) (&wcnt[0][0])[k] = 0u;
-        __syncthreads();
+    auto group_of = [&](uint64_t i) -> int {
+        return i < (uint64_t)kOrderCache ? (int)s_g[i] : length_group(ranges[2 * i + 1] - ranges[2 * i]);
+    };
+    const uint64_t chunk = ((uint64_t)T + NW - 1) / NW;
+    const uint64_t lo = (uint64_t)warp * chunk < T ? (uint64_t)warp * chunk : (uint64_t)T;
+    const uint64_t hi = lo + chunk < T ? lo + chunk : (uint64_t)T;
+    const uint32_t below = (1u << lane) - 1u;
+
+    for (uint64_t c = lo; c < hi; c += 32) {   // 1: this warp's count per group
+        const uint64_t i = c + lane;
+        const bool valid = i < hi;
+        const int g = valid ? group_of(i) : kOrderGroups + lane;
         const uint32_t peers = __match_any_sync(0xffffffffu, g);
-        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][g] = __popc(peers);
-        __syncthreads();
-        if (t < kOrderGroups) {   // exclusive prefix over the warps, per group, after the group's cursor
-            uint32_t run = cursor[t];
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t c = wcnt[w][t];
-                wcnt[w][t] = run;
-                run += c;
-            }
-            cursor[t] = run;
+        if (valid && lane == __ffs(peers) - 1) s_cur[warp][g] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int g = warp; g < kOrderGroups; g += NW) {   // 2: per group, exclusive prefix over the warps
+        const uint32_t v = s_cur[lane][g];
+        uint32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
         }
-        __syncthreads();
-        if (valid) order[wcnt[warp][g] + rank] = i;
-        __syncthreads();
+        s_cur[lane][g] = x - v;
+        if (lane == 31) s_base[g] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {   // 3: group starts, longest first: lane l takes group 32 - l, group 0 comes last
+        const uint32_t v = s_base[32 - lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t nonempty = __shfl_sync(0xffffffffu, x, 31);
+        __syncwarp();
+        s_base[32 - lane] = x - v;
+        if (lane == 0) s_base[0] = nonempty;
+    }
+    __syncthreads();
+    for (uint64_t c = lo; c < hi; c += 32) {   // 4: place this warp's tiles in order
+        const uint64_t i = c + lane;
+        const bool valid = i < hi;
+        const int g = valid ? group_of(i) : kOrderGroups + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, g);
+        const uint32_t slot = valid ? s_base[g] + s_cur[warp][g] + __popc(peers & below) : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) s_cur[warp][g] += __popc(peers);
+        __syncwarp();
+        if (valid) order[slot] = (uint32_t)i;
     }
 }
 

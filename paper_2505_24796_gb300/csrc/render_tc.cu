@@ -555,6 +555,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 const float4* sP = reinterpret_cast<const float4*>(smem + kSmemP + (k % 3u) * kPBytes);
                 uint32_t m = __all_sync(0xffffffffu, done) ? 0u : mask_cur;
                 if (kStats) cols += __popc(m);
+                const uint32_t pbase = b0 + 1u - start;   // 1 + list index of column 0
                 while (m) {
                     const int j = __ffs(m) - 1;
                     m &= m - 1;
@@ -574,15 +575,15 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                     C1 = fmaf(c.y, w, C1);
                     C2 = fmaf(c.z, w, C2);
                     T = blend ? Tn : T;
-                    const uint32_t pos = b0 + (uint32_t)j + 1u - start;
+                    const uint32_t pos = pbase + (uint32_t)j;
                     last = blend ? pos : last;
                     if (kStats) {
                         n_eval = term ? pos : n_eval;
                         n_blend += blend ? 1u : 0u;
                     }
                     thr = term ? kInf : thr;
-                    done = done || term;
                 }
+                done = thr == kInf;   // terminated (thr starts infinite for pixels outside the image)
             }
             walked = (k + 1) * kN;
             tc_fence_before();

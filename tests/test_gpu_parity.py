@@ -356,6 +356,29 @@ def test_persistent_render_matches_one_cta_per_tile(tc, name, make):
     assert (np.diff(order)[same] > 0).all()   # tile order inside a group
 
 
+@pytest.mark.parametrize("width,height", [(40, 24), (1920, 1080), (4160, 2176)])
+def test_tile_order_is_the_stable_longest_first_sort(tc, width, height):
+    """tcgs_tile_order on synthetic list lengths spanning every length group (empty lists up to
+    2^32 - 1 entries), on grids from 6 tiles to one past the kernel's shared-memory cache of 32768
+    tiles: the order is the stable sort of the tiles by descending floor(log2(length)) + 1."""
+    cam = scenes.pinhole(width, height, 1000.0)
+    nt = ((width + 15) // 16) * ((height + 15) // 16)
+    rng = np.random.default_rng(nt)
+    g = rng.integers(0, 33, nt)
+    lo = np.where(g > 0, np.left_shift(np.ones(nt, np.uint64), np.maximum(g, 1).astype(np.uint64) - 1), 0)
+    lens = lo + (rng.random(nt) * lo).astype(np.uint64)          # inside [2^(g-1), 2^g)
+    starts = rng.integers(0, 2**32, nt, dtype=np.uint64)
+    ranges = np.stack([starts, (starts + lens) % 2**32], axis=1).astype(np.uint32)
+    out = tc.tcgs_tile_order(cam, torch.from_numpy(ranges.view(np.int32)).to(DEV))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    lens32 = (ranges[:, 1] - ranges[:, 0]).astype(np.int64)
+    assert (lens32 == lens.astype(np.int64)).all()
+    groups = np.where(lens32 > 0, np.floor(np.log2(np.maximum(lens32, 1))).astype(np.int64) + 1, 0)
+    np.testing.assert_array_equal(groups, g)
+    np.testing.assert_array_equal(got, np.argsort(-groups, kind="stable"))
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
