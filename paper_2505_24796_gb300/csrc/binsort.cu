@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
                                                          const uint32_t* n_dev, int shift, uint32_t mask, int G,
                                                          uint32_t* __restrict__ hist,
                                                          uint32_t* __restrict__ digit_total) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ uint32_t h[kWarps][kRadix];
     const int t = threadIdx.x, warp = t >> 5;
 #pragma unroll
@@ -101,6 +103,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
 __global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ hist,
                                                          const uint32_t* __restrict__ digit_total,
                                                          uint32_t* __restrict__ digit_total_next, int G) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ uint32_t ws[kWarps];
     const int d = blockIdx.x, t = threadIdx.x;
     uint32_t tot;
@@ -132,6 +136,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
                                                             uint32_t* __restrict__ vals_out, uint32_t n_host,
                                                             const uint32_t* n_dev, int shift, uint32_t mask, int G,
                                                             const uint32_t* __restrict__ offsets) {
+    pdl_trigger();
+    pdl_wait();
     constexpr int TI = kThreads * KI;
     __shared__ uint32_t wcnt[kWarps][kRadix];
     __shared__ uint32_t boff[kRadix];     // next global position of each digit for this block
@@ -365,6 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, con
                                                        uint32_t* __restrict__ vals, uint32_t* __restrict__ counts,
                                                        uint32_t* __restrict__ ranges, int n_range_words,
                                                        uint32_t* __restrict__ digit_total0) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0) digit_total0[threadIdx.x] = 0u;
     if (i < n_range_words) ranges[i] = 0u;
@@ -400,6 +407,8 @@ __global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, con
 __global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ counts,
                                                           const uint32_t* __restrict__ order, uint32_t P, int G2,
                                                           unsigned long long* __restrict__ block_sums) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ unsigned long long ws[kWarps];
     uint32_t per = (P + G2 - 1) / G2;
     uint64_t lo = (uint64_t)blockIdx.x * per, hi = lo + per;
@@ -414,6 +423,8 @@ __global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __rest
 __global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* __restrict__ block_sums, int G2,
                                                    int64_t capacity, int64_t* __restrict__ n_splats,
                                                    int32_t* __restrict__ status, uint32_t* __restrict__ n_u32) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ unsigned long long ws[32];
     int t = threadIdx.x;
     unsigned long long x = t < G2 ? block_sums[t] : 0ull;
@@ -433,6 +444,8 @@ __global__ void __launch_bounds__(kThreads) k_scan_final(const uint32_t* __restr
                                                          const unsigned long long* __restrict__ block_sums,
                                                          uint32_t* __restrict__ offsets,
                                                          const uint32_t* __restrict__ n_u32) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ unsigned long long ws[kWarps];
     uint32_t per = (P + G2 - 1) / G2;
     uint64_t lo = (uint64_t)blockIdx.x * per, hi = lo + per;
@@ -465,6 +478,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
                                                         const float* __restrict__ opacity,
                                                         uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ n_u32) {
+    pdl_wait();
     __shared__ BlockCover s_bc;
     __shared__ uint32_t s_g[kThreads];
     __shared__ uint32_t s_off[kThreads], s_used[kThreads];
@@ -528,6 +542,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
 __global__ void __launch_bounds__(kThreads) k_ranges(const uint32_t* __restrict__ tile_keys,
                                                      const uint32_t* __restrict__ n_u32,
                                                      uint32_t* __restrict__ ranges) {
+    pdl_wait();
     const uint32_t n = *n_u32;
     const uint32_t quads = (n + 3) / 4;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += gridDim.x * blockDim.x) {
@@ -622,11 +637,11 @@ inline void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
     uint32_t* tot = w.digit_total + (pass & 1) * kRadix;
     uint32_t* nxt = w.digit_total + ((pass + 1) & 1) * kRadix;
     const uint32_t mask = (1u << bits) - 1u;
-    k_radix_hist<KI><<<G, kThreads, 0, s>>>(kin, n_host, n_dev, shift, mask, G, w.hist, tot);
+    launch_pdl(k_radix_hist<KI>, G, kThreads, 0, s, kin, n_host, n_dev, shift, mask, G, w.hist, tot);
     count_launches(1);
-    k_radix_scan<<<kRadix, kThreads, 0, s>>>(w.hist, tot, nxt, G);
+    launch_pdl(k_radix_scan, kRadix, kThreads, 0, s, w.hist, tot, nxt, G);
     count_launches(1);
-    k_radix_scatter<KI><<<G, kThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, mask, G, w.hist);
+    launch_pdl(k_radix_scatter<KI>, G, kThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift, mask, G, w.hist);
     count_launches(1);
 }
 
@@ -664,11 +679,11 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     if (n_init < kThreads) n_init = kThreads;
     const int kb_blocks = (n_init + kThreads - 1) / kThreads;
     if (exact)
-        k_bin_keys<true><<<kb_blocks, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, conic, opacity, w.dk_a, w.dv_a,
-                                                       w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
+        launch_pdl(k_bin_keys<true>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
+                   w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
     else
-        k_bin_keys<false><<<kb_blocks, kThreads, 0, s>>>(dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
-                                                        w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
+        launch_pdl(k_bin_keys<false>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
+                   w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 1. depth order (4 passes; the result returns to the a-buffers)
@@ -686,14 +701,19 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     // 2. offsets, N, capacity check
     int G2 = P < kScanBlocks * 256 ? (P + 255) / 256 : kScanBlocks;
     if (G2 < 1) G2 = 1;
-    if (P > 0) k_scan_reduce<<<G2, kThreads, 0, s>>>(w.counts, order, (uint32_t)P, G2, w.block_sums);
-    if (P > 0) count_launches(1);
-    else cudaMemsetAsync(w.block_sums, 0, 8, s);
-    k_scan_top<<<1, 1024, 0, s>>>(w.block_sums, G2, splat_capacity, n_splats, status, w.n_u32);
-    count_launches(1);
-    if (P > 0)
-        k_scan_final<<<G2, kThreads, 0, s>>>(w.counts, order, (uint32_t)P, G2, w.block_sums, w.offsets, w.n_u32);
+    if (P > 0) {
+        launch_pdl(k_scan_reduce, G2, kThreads, 0, s, w.counts, order, (uint32_t)P, G2, w.block_sums);
         count_launches(1);
+    } else {
+        cudaMemsetAsync(w.block_sums, 0, 8, s);
+    }
+    launch_pdl(k_scan_top, 1, 1024, 0, s, w.block_sums, G2, splat_capacity, n_splats, status, w.n_u32);
+    count_launches(1);
+    if (P > 0) {
+        launch_pdl(k_scan_final, G2, kThreads, 0, s, w.counts, order, (uint32_t)P, G2, w.block_sums, w.offsets,
+                   w.n_u32);
+        count_launches(1);
+    }
     TCGS_CHECK_LAUNCH();
     if (splat_capacity == 0 || P == 0) return TCGS_OK;
     // 3. duplication into the buffer the first tile pass reads
@@ -705,11 +725,11 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     int src = (tpasses & 1) ? 1 : 0;
     const int dup_blocks = (P + kThreads - 1) / kThreads;
     if (exact)
-        k_duplicate<true><<<dup_blocks, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts, mean2d, radius,
-                                                         conic, opacity, kbuf[src], vbuf[src], w.n_u32);
+        launch_pdl(k_duplicate<true>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
+                   radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
     else
-        k_duplicate<false><<<dup_blocks, kThreads, 0, s>>>(dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
-                                                          radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
+        launch_pdl(k_duplicate<false>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
+                   radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     // 4. stable sort by tile id, 8 bits per pass (an even split of the tile bits measured slower)
@@ -724,7 +744,7 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     TCGS_CHECK_LAUNCH();
     // 5. ranges
     int Gr = sort_blocks<kItemsSplat>(splat_capacity) * 4;
-    k_ranges<<<Gr, kThreads, 0, s>>>(kbuf[src], w.n_u32, tile_ranges);
+    launch_pdl(k_ranges, Gr, kThreads, 0, s, kbuf[src], w.n_u32, tile_ranges);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
@@ -772,6 +792,7 @@ static_assert(kOrderGroups == 33 && kOrderThreads == 1024, "the scans below take
 
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t* __restrict__ ranges, uint32_t T,
                                                              uint32_t* __restrict__ order) {
+    pdl_wait();
     constexpr int NW = kOrderThreads / 32;
     __shared__ uint8_t s_g[kOrderCache];
     __shared__ uint32_t s_cur[NW][kOrderGroups];   // this warp's tiles of a group, then its next slot there
@@ -848,7 +869,7 @@ extern "C" tcgs_status tcgs_tile_order(const tcgs_camera* cam, const uint32_t* t
     const DevCamera dc = make_dev_camera(*cam);
     const uint64_t T = (uint64_t)dc.grid_w * dc.grid_h;
     if (T > 0xFFFFFFFFull) return TCGS_ERR_INVALID;
-    k_tile_order<<<1, kOrderThreads, 0, (cudaStream_t)stream>>>(tile_ranges, (uint32_t)T, tile_order);
+    launch_pdl(k_tile_order, 1, kOrderThreads, 0, (cudaStream_t)stream, tile_ranges, (uint32_t)T, tile_order);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
@@ -863,6 +884,7 @@ __global__ void __launch_bounds__(kThreads) k_order_keys(const float* __restrict
                                                          const uint32_t* __restrict__ items, int n,
                                                          uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                          uint32_t* __restrict__ digit_total0) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0) digit_total0[threadIdx.x] = 0u;
     if (i >= n) return;
@@ -905,7 +927,7 @@ extern "C" tcgs_status tcgs_sched_order(const float* cost, const uint32_t* items
     OrderWs o = order_layout((char*)workspace, n);
     if (ws_bytes < o.bytes) return TCGS_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    k_order_keys<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(cost, items, n, o.k0, o.v0, o.digit_total);
+    launch_pdl(k_order_keys, (n + kThreads - 1) / kThreads, kThreads, 0, s, cost, items, n, o.k0, o.v0, o.digit_total);
     count_launches(1);
     Workspace w = {};
     w.hist = o.hist;

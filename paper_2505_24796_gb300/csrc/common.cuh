@@ -120,6 +120,30 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Programmatic dependent launch: a kernel started with launch_pdl may be scheduled while the kernel
+// before it in the stream drains; it calls pdl_wait() before its first global memory access, which
+// returns once that kernel has completed and its writes are visible (at once after a plain launch).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel in the stream be scheduled now rather than when this block exits (for
+// kernels whose blocks all fit on the GPU at once, so early arrivals take no slot they need).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 __device__ __forceinline__ void set_status(int32_t* st, int code) {
     if (st) atomicCAS(st, 0, code);
 }

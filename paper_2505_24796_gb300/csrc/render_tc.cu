@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     tc_fence_before();
     __syncthreads();   // U visible to the tensor core, TMEM address and mbarriers published
     tc_fence_after();
+    pdl_wait();        // the set-up above touches no global memory; the tiles below do
     const uint32_t tmem = s_tmem;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const float kInf = __int_as_float(0x7f800000);
@@ -651,6 +652,18 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     }
 }
 
+// The work-queue counter is zeroed by a one-thread kernel rather than a memset, so that the
+// launches on either side of it stay programmatic (a memset between two kernels would serialise them).
+__global__ void k_zero_counter(uint32_t* c) {
+    pdl_wait();
+    *c = 0u;
+}
+
+void zero_counter(uint32_t* c, cudaStream_t s) {
+    launch_pdl(k_zero_counter, 1, 1, 0, s, c);
+    count_launches(1);
+}
+
 int g_checked_device = -1;
 bool g_device_ok = false;
 int g_sm_count = 0;
@@ -678,7 +691,7 @@ tcgs_status launch_tc_t(const TcParams& p, int blocks, cudaStream_t s) {
             return TCGS_ERR_CUDA;
         g_attr_set[kInspect][kStats][kQueue][kEarly][kSplit] = true;
     }
-    kern<<<blocks, kTcThreads, kSmemDyn, s>>>(p);
+    launch_pdl(kern, blocks, kTcThreads, kSmemDyn, s, p);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
@@ -760,7 +773,7 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
         p.queue_tiles = 1;
         p.n_items = (uint32_t)tiles;
         p.counter = opts->work_counter;
-        if (cudaMemsetAsync(opts->work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return TCGS_ERR_CUDA;
+        zero_counter(opts->work_counter, s);
         int ctas = g_sm_count * kTcCtasPerSm;
         if (ctas > tiles) ctas = tiles;
         return opts->tile_stats ? launch_tc<false, true, true>(p, ctas, s) : launch_tc<false, false, true>(p, ctas, s);
@@ -838,7 +851,7 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     p.n_items = (uint32_t)n_items;
     p.counter = work_counter;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return TCGS_ERR_CUDA;
+    zero_counter(work_counter, s);
     bool any_stats = false;
     for (int v = 0; v < n_views; ++v) any_stats = any_stats || views[v].tile_stats;
     // persistent grid: at most the CTAs that are resident at once (4 per SM for this kernel)
