@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(DevCamera cam, int P, 
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     __shared__ float4 s_sh[kStageSh ? kProjThreads / 32 : 1][kStageSh ? 32 * kShRow4 : 1];
     if (kStageSh) {
-        // the warp's degree-3 rows, coalesced: float4 i of the warp's block goes to row i / 12
+        // the warp's degree-3 rows, coalesced, copied asynchronously (no registers held): float4 i
+        // of the warp's block goes to row i / 12
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int g0 = g - lane;
         const int rows = P - g0 < 32 ? P - g0 : 32;
@@ -66,13 +67,28 @@ __global__ void __launch_bounds__(kProjThreads) k_project(DevCamera cam, int P, 
 #pragma unroll
             for (int m = 0; m < 12; ++m) {
                 const int i = lane + 32 * m;
-                if (i < 12 * rows) s_sh[warp][(i / 12) * kShRow4 + i % 12] = src[i];
+                if (i < 12 * rows) {
+                    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_sh[warp][(i / 12) * kShRow4 + i % 12]);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
+                }
             }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // every other input of this Gaussian is requested before the staged rows are waited for
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, op = 1.f;
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (g < P) {
+        m0 = means3[3 * g]; m1 = means3[3 * g + 1]; m2 = means3[3 * g + 2];
+        q = *reinterpret_cast<const float4*>(quats + 4 * (size_t)g);
+        s0 = scales[3 * g]; s1 = scales[3 * g + 1]; s2 = scales[3 * g + 2];
+        if (opacity) op = opacity[g];
+    }
+    if (kStageSh) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
     }
     if (g >= P) return;
-    float m0 = means3[3 * g], m1 = means3[3 * g + 1], m2 = means3[3 * g + 2];
     // camera-space mean t = W mu
     float tx = cam.R[0] * m0 + cam.R[1] * m1 + cam.R[2] * m2 + cam.t[0];
     float ty = cam.R[3] * m0 + cam.R[4] * m1 + cam.R[5] * m2 + cam.t[1];
@@ -85,10 +101,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(DevCamera cam, int P, 
 
     if (tz > cam.near_z) {
         // Sigma = M M^T with M = R(q) diag(s)
-        float4 q = *reinterpret_cast<const float4*>(quats + 4 * (size_t)g);
         float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
         float w = q.x * qn, x = q.y * qn, y = q.z * qn, z = q.w * qn;
-        float s0 = scales[3 * g], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
         float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
                        2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                        2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
@@ -124,7 +138,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(DevCamera cam, int P, 
         float det = a * c - b * b;
         // squared reach in units of sigma: 9 for the 3-sigma square, 2 ln(255 o) for the square
         // bounding the ellipse where alpha >= 1/255 (Eq. 5); o <= 1/255 reaches no pixel
-        const float reach2 = opacity ? 2.f * logf(255.f * opacity[g]) : 9.f;
+        const float reach2 = opacity ? 2.f * logf(255.f * op) : 9.f;
         if (det > 0.f && reach2 > 0.f) {
             float mid = 0.5f * (a + c);
             float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
@@ -143,11 +157,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project(DevCamera cam, int P, 
                 float dx = m0 - cam.campos[0], dy = m1 - cam.campos[1], dz = m2 - cam.campos[2];
                 float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
                 float Y[16];
-                sh_basis(deg, dx * dn, dy * dn, dz * dn, Y);
+                sh_basis(kStageSh ? 3 : deg, dx * dn, dy * dn, dz * dn, Y);   // staged rows are degree 3
                 int K = (deg + 1) * (deg + 1);
                 float cr = 0.5f, cg = 0.5f, cb = 0.5f;
                 const float* s = sh + (size_t)g * K * 3;
-                if (deg == 3) {
+                if (kStageSh || deg == 3) {
                     const float4* s4 = kStageSh ? &s_sh[threadIdx.x >> 5][(threadIdx.x & 31) * kShRow4]
                                                 : reinterpret_cast<const float4*>(s);
                     float v[48];
