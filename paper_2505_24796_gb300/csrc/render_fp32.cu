@@ -114,10 +114,13 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_fp32(FwdParams p) {
 
 // ---------------------------------------------------------------- backward
 //
-// One CTA per tile, one thread per pixel.  Each pixel replays its fragments 0 .. n_contrib-1
-// front to back with the forward's FP32 alpha arithmetic, so T_j matches the forward bit for
-// bit; the colour blended after fragment j is img - bg T_final - (prefix up to j).  Per
-// Gaussian, the 9 gradient terms of a warp's pixels are summed with shuffles before one lane
+// One CTA per tile, one thread per pixel; each warp owns an 8 x 4 pixel block.  Each pixel replays
+// its fragments 0 .. n_contrib-1 front to back with the forward's FP32 alpha arithmetic, so T_j
+// matches the forward bit for bit; the colour blended after fragment j is img - bg T_final -
+// (prefix up to j).  A warp replays only the fragments that can reach alpha >= 1/255 somewhere in
+// its block (the exact minimum of the conic form over the block's pixel centres against the reach
+// limit, as the tensor-core forward marks them): the others contribute to no pixel of the block.
+// Per Gaussian, the 9 gradient terms of a warp's pixels are summed with shuffles before the block
 // issues the atomics.
 
 struct BwdParams {
@@ -147,18 +150,51 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Gradient partial sums of a fragment: each warp reduces its 32 pixels' contributions with shuffles
-// and parks the 9 sums in shared memory; every kBwdChunk fragments the block adds the 8 warps' sums
-// and issues one global atomic per (fragment, parameter) -- 8 times fewer same-address atomics than
-// one per warp.
+// Sums v[0..8] over the warp and stores the 9 totals in part[0..8].  v[0..7] take a transposing
+// butterfly: at each of the first three levels a lane keeps half of its values and sends the other
+// half to its partner, so that after them lane l holds a partial sum of one value,
+// 4 bit4(l) + 2 bit3(l) + bit2(l), which two more levels complete (9 shuffles for the 8 values
+// instead of 40); v[8] takes the plain 5-level sum.
+__device__ __forceinline__ void warp_sum9_store(const float (&v)[9], float* part) {
+    const int lane = threadIdx.x & 31;
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = u16 ? v[i] : v[i + 4], keep = u16 ? v[i + 4] : v[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = u8 ? w[i] : w[i + 2], keep = u8 ? w[i + 2] : w[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float y;
+    {
+        const float send = u4 ? x[0] : x[1], keep = u4 ? x[1] : x[0];
+        y = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    const float z = warp_sum(v[8]);
+    if ((lane & 3) == 0) part[(u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0)] = y;
+    if (lane == 0) part[8] = z;
+}
+
+// Gradient partial sums of a fragment: each warp parks its 9 sums in shared memory (slots of
+// fragments it does not replay, or to which none of its pixels contributes, stay zero); every
+// kBwdChunk fragments the block adds the 8 warps' sums, clears the slots, and issues one global
+// atomic per nonzero (fragment, parameter) -- 8 times fewer same-address atomics than one per warp.
 constexpr int kBwdChunk = 32;
 constexpr int kBwdWarps = kFwdThreads / 32;
 constexpr int kBwdParams = 9;   // dmean2d (2), dconic (3), dopacity, drgb (3)
 
 __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
     __shared__ float2 s_xy[kFwdThreads];
-    __shared__ float4 s_co[kFwdThreads];
-    __shared__ float4 s_rgb[kFwdThreads];
+    __shared__ float4 s_co[kFwdThreads];   // sigma11, sigma12, sigma22, opacity
+    __shared__ float4 s_rgb[kFwdThreads];  // r, g, b, reach limit
+    __shared__ float4 s_inv[kFwdThreads];  // 1 / sigma11, 1 / sigma22, ln(opacity)
     __shared__ uint32_t s_id[kFwdThreads];
     __shared__ uint32_t s_max;
     __shared__ float s_part[kBwdChunk][kBwdWarps][kBwdParams];
@@ -166,9 +202,14 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
     const int tile = blockIdx.x;
     const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
     const int t = threadIdx.x, lane = t & 31;
-    const int px_i = tx * kTile + (t & 15), py_i = ty * kTile + (t >> 4);
+    const int bx = warp & 1, by = warp >> 1;
+    const int lx = 8 * bx + (lane & 7), ly = 4 * by + (lane >> 3);
+    const int px_i = tx * kTile + lx, py_i = ty * kTile + ly;
     const bool inside = px_i < p.cam.width && py_i < p.cam.height;
     const float px = px_i + 0.5f, py = py_i + 0.5f;
+    // the warp's pixel-centre rectangle relative to the tile centre
+    const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);
+    const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f, by0 = 4.f * by - 7.5f, by1 = by0 + 3.f;
     const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
 
     uint32_t nc = 0;
@@ -184,9 +225,11 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
         R1 = p.img[plane + pix] - Tf * p.bg[1];
         R2 = p.img[2 * plane + pix] - Tf * p.bg[2];
     }
+    const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc);
     if (t == 0) s_max = 0;
+    for (int q = t; q < kBwdChunk * kBwdWarps * kBwdParams; q += kFwdThreads) (&s_part[0][0][0])[q] = 0.f;
     __syncthreads();
-    atomicMax(&s_max, nc);
+    if (lane == 0) atomicMax(&s_max, warp_nc);
     __syncthreads();
     const uint32_t span = s_max;
     float T = 1.f;
@@ -195,79 +238,88 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
         uint32_t idx = start + b0 + t;
         if (idx < end) {
             uint32_t g = p.ids[idx];
+            const float o = p.opacity[g];
+            const float a = p.conic[3 * g], c = p.conic[3 * g + 2];
             s_id[t] = g;
             s_xy[t] = reinterpret_cast<const float2*>(p.mean2d)[g];
-            s_co[t] = make_float4(p.conic[3 * g], p.conic[3 * g + 1], p.conic[3 * g + 2], p.opacity[g]);
-            s_rgb[t] = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], 0.f);
+            s_co[t] = make_float4(a, p.conic[3 * g + 1], c, o);
+            const float lno = __logf(o);
+            s_rgb[t] = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], reach_limit(lno));
+            s_inv[t] = make_float4(__fdividef(1.f, a), __fdividef(1.f, c), lno, 0.f);
         }
         __syncthreads();
-        uint32_t nb = span - b0 < (uint32_t)kFwdThreads ? span - b0 : (uint32_t)kFwdThreads;
-        for (uint32_t j = 0; j < nb; ++j) {
-            float dm0 = 0.f, dm1 = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dop = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
-            bool contrib = false;
-            if (b0 + j < nc) {
-                float2 m = s_xy[j];
-                float4 co = s_co[j];
-                float dx = m.x - px, dy = m.y - py;
-                float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                float G = expf(power);
-                float raw = co.w * G;
-                float alpha = fminf(p.alpha_max, raw);
-                bool early = p.early_cull && power + __logf(co.w) < kBetaCull;   // same test as the forward
-                if (!early && alpha >= kCullAlpha) {
-                    contrib = true;
-                    float4 c = s_rgb[j];
-                    float w = alpha * T;
-                    dr0 = w * g0; dr1 = w * g1; dr2 = w * g2;
-                    R0 -= c.x * w; R1 -= c.y * w; R2 -= c.z * w;
-                    float ia = 1.f / (1.f - alpha);
-                    float dL_da = g0 * (c.x * T - (R0 + Tf * p.bg[0]) * ia) +
-                                  g1 * (c.y * T - (R1 + Tf * p.bg[1]) * ia) +
-                                  g2 * (c.z * T - (R2 + Tf * p.bg[2]) * ia);
-                    if (raw <= p.alpha_max) {
-                        float dL_dp = dL_da * alpha;
-                        dop = dL_da * G;
-                        dm0 = -dL_dp * (co.x * dx + co.y * dy);
-                        dm1 = -dL_dp * (co.y * dx + co.z * dy);
-                        dc0 = -0.5f * dL_dp * dx * dx;
-                        dc1 = -dL_dp * dx * dy;
-                        dc2 = -0.5f * dL_dp * dy * dy;
+        const uint32_t nb = span - b0 < (uint32_t)kFwdThreads ? span - b0 : (uint32_t)kFwdThreads;
+        for (uint32_t c0 = 0; c0 < nb; c0 += kBwdChunk) {
+            // this warp's fragments of the chunk: in some pixel's replay range and able to reach the block
+            const uint32_t jl = c0 + (uint32_t)lane;
+            bool mk = jl < nb && b0 + jl < warp_nc;
+            if (mk) {
+                const float2 m = s_xy[jl];
+                const float4 co = s_co[jl];
+                const float4 inv = s_inv[jl];
+                const float lim = s_rgb[jl].w;
+                mk = lim >= 0.f &&
+                     min_q_box_facing(m.x - cx, m.y - cy, co.x, co.y, co.z, inv.x, inv.y, bx0, bx1, by0, by1) <= lim;
+            }
+            uint32_t marks = __ballot_sync(0xffffffffu, mk);
+            while (marks) {
+                const uint32_t j = c0 + (uint32_t)(__ffs(marks) - 1);
+                marks &= marks - 1;
+                float v[kBwdParams] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                bool contrib = false;
+                if (b0 + j < nc) {
+                    float2 m = s_xy[j];
+                    float4 co = s_co[j];
+                    float dx = m.x - px, dy = m.y - py;
+                    float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+                    float G = expf(power);
+                    float raw = co.w * G;
+                    float alpha = fminf(p.alpha_max, raw);
+                    bool early = p.early_cull && power + s_inv[j].z < kBetaCull;   // same test as the forward
+                    if (!early && alpha >= kCullAlpha) {
+                        contrib = true;
+                        float4 c = s_rgb[j];
+                        float w = alpha * T;
+                        v[6] = w * g0; v[7] = w * g1; v[8] = w * g2;
+                        R0 -= c.x * w; R1 -= c.y * w; R2 -= c.z * w;
+                        float ia = 1.f / (1.f - alpha);
+                        float dL_da = g0 * (c.x * T - (R0 + Tf * p.bg[0]) * ia) +
+                                      g1 * (c.y * T - (R1 + Tf * p.bg[1]) * ia) +
+                                      g2 * (c.z * T - (R2 + Tf * p.bg[2]) * ia);
+                        if (raw <= p.alpha_max) {
+                            float dL_dp = dL_da * alpha;
+                            v[5] = dL_da * G;
+                            v[0] = -dL_dp * (co.x * dx + co.y * dy);
+                            v[1] = -dL_dp * (co.y * dx + co.z * dy);
+                            v[2] = -0.5f * dL_dp * dx * dx;
+                            v[3] = -dL_dp * dx * dy;
+                            v[4] = -0.5f * dL_dp * dy * dy;
+                        }
+                        T = fmaf(-alpha, T, T);
                     }
-                    T = fmaf(-alpha, T, T);
                 }
+                if (__any_sync(0xffffffffu, contrib)) warp_sum9_store(v, s_part[j - c0][warp]);
             }
-            float* part = s_part[j % kBwdChunk][warp];
-            if (__any_sync(0xffffffffu, contrib)) {
-                dm0 = warp_sum(dm0); dm1 = warp_sum(dm1);
-                dc0 = warp_sum(dc0); dc1 = warp_sum(dc1); dc2 = warp_sum(dc2);
-                dop = warp_sum(dop);
-                dr0 = warp_sum(dr0); dr1 = warp_sum(dr1); dr2 = warp_sum(dr2);
-                if (lane == 0) {
-                    part[0] = dm0; part[1] = dm1; part[2] = dc0; part[3] = dc1; part[4] = dc2;
-                    part[5] = dop; part[6] = dr0; part[7] = dr1; part[8] = dr2;
-                }
-            } else if (lane < kBwdParams) {
-                part[lane] = 0.f;
-            }
-            if ((j + 1) % kBwdChunk == 0 || j + 1 == nb) {
-                // the block adds the warps' sums of the chunk's fragments: one atomic per value
-                __syncthreads();
-                const uint32_t j0 = j - j % kBwdChunk, nf = j + 1 - j0;
-                for (uint32_t q = threadIdx.x; q < nf * kBwdParams; q += kFwdThreads) {
-                    const uint32_t f = q / kBwdParams, k = q - f * kBwdParams;
-                    float v = 0.f;
+            // the block adds the warps' sums of the chunk's fragments: one atomic per value
+            __syncthreads();
+            const uint32_t nf = nb - c0 < (uint32_t)kBwdChunk ? nb - c0 : (uint32_t)kBwdChunk;
+            for (uint32_t q = threadIdx.x; q < nf * kBwdParams; q += kFwdThreads) {
+                const uint32_t f = q / kBwdParams, k = q - f * kBwdParams;
+                float sum = 0.f;
 #pragma unroll
-                    for (int w = 0; w < kBwdWarps; ++w) v += s_part[f][w][k];
-                    if (v != 0.f) {
-                        const uint32_t g = s_id[j0 + f];
-                        float* dst = k < 2 ? &p.dmean2d[2 * g + k]
-                                           : (k < 5 ? &p.dconic[3 * g + (k - 2)]
-                                                    : (k == 5 ? &p.dopacity[g] : &p.drgb[3 * g + (k - 6)]));
-                        atomicAdd(dst, v);
-                    }
+                for (int w = 0; w < kBwdWarps; ++w) {
+                    sum += s_part[f][w][k];
+                    s_part[f][w][k] = 0.f;
                 }
-                __syncthreads();
+                if (sum != 0.f) {
+                    const uint32_t g = s_id[c0 + f];
+                    float* dst = k < 2 ? &p.dmean2d[2 * g + k]
+                                       : (k < 5 ? &p.dconic[3 * g + (k - 2)]
+                                                : (k == 5 ? &p.dopacity[g] : &p.drgb[3 * g + (k - 6)]));
+                    atomicAdd(dst, sum);
+                }
             }
+            __syncthreads();
         }
     }
 }

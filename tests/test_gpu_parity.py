@@ -129,10 +129,11 @@ def test_bin_sort_capacity_overflow_reports_status(tc):
     n = int(pr["tiles_touched"].sum())
     m = to_torch(f32(pr["mean2d"]), DEV); r = to_torch(pr["radius"].astype(np.int32), DEV)
     d = to_torch(f32(pr["depth"]), DEV)
-    out = tc.tcgs_bin_sort(cam, m, r, d, capacity=n - 1)
-    torch.cuda.synchronize()
-    assert int(out["status"].item()) == 3 and int(out["n_splats"].item()) == n
-    assert (out["tile_ranges"][:, 0] == out["tile_ranges"][:, 1]).all()
+    for cap in (n - 1, 1, 0):   # N is still counted (by the duplication's last block) when nothing fits
+        out = tc.tcgs_bin_sort(cam, m, r, d, capacity=cap)
+        torch.cuda.synchronize()
+        assert int(out["status"].item()) == 3 and int(out["n_splats"].item()) == n
+        assert (out["tile_ranges"][:, 0] == out["tile_ranges"][:, 1]).all()
 
 
 def test_bin_sort_empty_and_all_culled(tc):
