@@ -16,6 +16,7 @@
 // rounds with __match_any_sync, warps and tiles are chained in order, so the pass is stable.
 // No block ever waits on another block.
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -289,6 +290,13 @@ struct BlockCover {
     uint32_t total;
 };
 
+// BlockCover with the exact coverage of wide Gaussians by tile rows (see stage_block_exact).
+struct BlockCoverRows : BlockCover {
+    uint32_t rpre[kThreads];     // exclusive prefix of the row counts
+    unsigned long long wsum64[kWarps];
+    uint32_t total_rows;
+};
+
 // Stages thread t's Gaussian g (valid) and returns its rectangle size; sets bc.total.  COVER: also
 // its coverage parameters (exact coverage).
 template <bool COVER = true>
@@ -359,11 +367,273 @@ __device__ __forceinline__ void block_cover_splats(BlockCover& bc, uint32_t grid
     }
 }
 
+// ---- exact coverage by tile rows
+//
+// In one row of tiles the tiles a Gaussian reaches form an interval: their pixel-centre boxes span
+// the same band of rows, and a box meets the convex region {q <= lim} exactly when its x-range meets
+// the region's shadow on the x axis within that band.  So each (Gaussian, tile row) is one unit of
+// work: the shadow's ends come from the ellipse in closed form, and the per-tile test (tile_reached)
+// fixes the interval's end tiles, so the tiles kept are those the per-tile test keeps (whenever they
+// form one run, which they do up to FP32 ties at the reach limit).  Narrow rows and degenerate
+// conics test every tile of the row and keep the run from the first to the last passing tile.
+
+// Extent of the reach ellipse {q <= lim} about the mean: half-widths W (x) and H (y), the y offset s
+// of its leftmost point (the rightmost one is at -s), and det = ac - b^2.  W < 0: scan the row.
+struct Reach {
+    float W, H, s, det;
+};
+
+__device__ __forceinline__ Reach reach_of(const Cover& v) {
+    Reach e;
+    e.det = __fsub_rn(__fmul_rn(v.a, v.c), __fmul_rn(v.b, v.b));
+    e.W = -1.f;
+    e.H = e.s = 0.f;
+    if (!(e.det > 0.f) || !(v.lim >= 0.f)) return e;
+    const float idet = __frcp_rn(e.det);
+    const float W = __fsqrt_rn(__fmul_rn(__fmul_rn(v.lim, v.c), idet));
+    const float H = __fsqrt_rn(__fmul_rn(__fmul_rn(v.lim, v.a), idet));
+    if (!(W < 1e30f) || !(H < 1e30f)) return e;
+    e.W = W;
+    e.H = H;
+    e.s = __fmul_rn(__fmul_rn(v.b, W), v.ic);
+    return e;
+}
+
+__device__ __forceinline__ int clamp_tile(float f, int lo, int hi) {
+    return (int)fminf(fmaxf(f, (float)lo), (float)hi);   // NaN -> lo
+}
+
+// Tiles [L, R] (empty when L > R) of rectangle columns [x0, x1] in tile row ty that Gaussian v reaches.
+__device__ int2 row_span(const Cover& v, const Reach& e, int ty, int x0, int x1) {
+    const int2 none = make_int2(1, 0);
+    if (!(v.lim >= 0.f)) return none;
+    const float ly = v.my - (float)(ty * kTile + kTile / 2);
+    auto test = [&](int tx) { return tile_reached(v, v.mx - (float)(tx * kTile + kTile / 2), ly); };
+    auto scan = [&]() {
+        int L = x0;
+        while (L <= x1 && !test(L)) ++L;
+        if (L > x1) return none;
+        int R = x1;
+        while (R > L && !test(R)) --R;
+        return make_int2(L, R);
+    };
+    if (e.W < 0.f || x1 - x0 < 3) return scan();
+    // the shadow [xa, xb] of the ellipse on the x axis within the row's band of pixel centres
+    const float yl = __fsub_rn((float)(ty * kTile) + 0.5f, v.my), yh = __fadd_rn(yl, 15.f);
+    float Lf = 1.f, Rf = 0.f;   // empty unless the band meets the ellipse
+    if (!(yl > e.H || yh < -e.H)) {
+        const float alim = __fmul_rn(v.a, v.lim);
+        const float dl = fminf(yh, fmaxf(yl, e.s)), dr = fminf(yh, fmaxf(yl, -e.s));
+        const float rl = __fsqrt_rn(fmaxf(0.f, __fsub_rn(alim, __fmul_rn(e.det, __fmul_rn(dl, dl)))));
+        const float rr = __fsqrt_rn(fmaxf(0.f, __fsub_rn(alim, __fmul_rn(e.det, __fmul_rn(dr, dr)))));
+        const float xa = __fmul_rn(__fsub_rn(__fmul_rn(-v.b, dl), rl), v.ia);
+        const float xb = __fmul_rn(__fadd_rn(__fmul_rn(-v.b, dr), rr), v.ia);
+        // tiles whose box [16 tx + 0.5, 16 tx + 15.5] meets [mx + xa, mx + xb]
+        Lf = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(v.mx, xa), 15.5f), 1.f / kTile));
+        Rf = floorf(__fmul_rn(__fsub_rn(__fadd_rn(v.mx, xb), 0.5f), 1.f / kTile));
+    }
+    if (!(Lf <= Rf) || Rf < (float)x0 || Lf > (float)x1) {
+        // no shadow in the rectangle: probe the tile holding the point of least q in the band (the
+        // least of the minima over x, (det / a) dy^2, is at the dy nearest to 0), grow from there
+        const float dyc = fminf(yh, fmaxf(yl, 0.f));
+        const float xc = __fadd_rn(v.mx, __fmul_rn(__fmul_rn(-v.b, dyc), v.ia));
+        const int c = clamp_tile(floorf(__fmul_rn(xc, 1.f / kTile)), x0, x1);
+        if (!test(c)) return none;
+        int L = c, R = c;
+        while (L > x0 && test(L - 1)) --L;
+        while (R < x1 && test(R + 1)) ++R;
+        return make_int2(L, R);
+    }
+    int L = clamp_tile(Lf, x0, x1), R = clamp_tile(Rf, x0, x1);
+    if (test(L)) {
+        while (L > x0 && test(L - 1)) --L;
+    } else {
+        int k = L + 1;
+        while (k <= R && !test(k)) ++k;
+        if (k > R) return scan();
+        L = k;
+    }
+    if (test(R)) {
+        while (R < x1 && test(R + 1)) ++R;
+    } else {
+        int k = R - 1;
+        while (k > L && !test(k)) --k;
+        R = k;
+    }
+    return make_int2(L, R);
+}
+
+// Gaussians whose rectangle is at least this many tiles wide are covered by rows; the narrower ones
+// tile by tile (for them a row costs about as many box tests as it has tiles, plus the row's own
+// bookkeeping).
+constexpr int kRowMinWidth = 6;
+// The row path runs when the caller's splat capacity allows at least this many splats per Gaussian.
+constexpr int kRowsCapacityPerGaussian = 32;
+// The binning kernels keep 8 blocks of 256 threads resident per SM (at most 32 registers a thread):
+// their tile path is bound by instruction latency and needs all 8; the row path, out of line, is
+// held to the same registers.
+constexpr int kCoverBlocksPerSm = 8;
+
+// Exact coverage staging: thread t's Gaussian g (valid) is covered by rows when its rectangle is at
+// least kRowMinWidth tiles wide, else tile by tile; a Gaussian that reaches no pixel (limit < 0) by
+// neither.  bc.rect holds every Gaussian's rectangle (a wide one with a zero tile count), bc.rpre the
+// prefix of the wide ones' row counts; one 64-bit scan forms both prefixes (rows in the high word:
+// a block's narrow tiles stay below 256 x 5 x 65536 and its rows below 256 x 65536).
+__device__ __forceinline__ void stage_block_exact(BlockCoverRows& bc, const DevCamera& cam, bool valid, uint32_t g,
+                                                  const float* __restrict__ mean2d,
+                                                  const int32_t* __restrict__ radius,
+                                                  const float* __restrict__ conic,
+                                                  const float* __restrict__ opacity) {
+    const int t = threadIdx.x;
+    uint32_t tiles = 0, rows = 0, x0 = 0, y0 = 0, rw = 1;
+    Cover cv{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1.f};
+    if (valid) {
+        const float2 m = reinterpret_cast<const float2*>(mean2d)[g];
+        const Rect rc = tile_rect(m.x, m.y, radius[g], cam.grid_w, cam.grid_h);
+        if (rect_count(rc)) {
+            cv = cover_of(mean2d, conic, opacity, g);
+            if (cv.lim >= 0.f) {
+                x0 = (uint32_t)rc.x0; y0 = (uint32_t)rc.y0; rw = (uint32_t)(rc.x1 - rc.x0 + 1);
+                if (rw >= (uint32_t)kRowMinWidth) rows = (uint32_t)(rc.y1 - rc.y0 + 1);
+                else tiles = rect_count(rc);
+            }
+        }
+    }
+    unsigned long long both;
+    const unsigned long long pre = block_exclusive_scan<unsigned long long, kThreads>(
+        ((unsigned long long)rows << 32) | tiles, bc.wsum64, both);
+    bc.cv[t] = cv;
+    bc.rect[t] = make_uint4(x0, y0, rw, (uint32_t)pre);
+    bc.inv_w[t] = 1.f / (float)rw;
+    bc.rpre[t] = (uint32_t)(pre >> 32);
+    if (t == 0) {
+        bc.total = (uint32_t)both;
+        bc.total_rows = (uint32_t)(both >> 32);
+    }
+    __syncthreads();
+}
+
+// Row `rr` (< total_rows) of the block: its Gaussian (thread index).
+__device__ __forceinline__ int row_owner(const BlockCoverRows& bc, uint32_t rr) {
+    int owner = 0;
+#pragma unroll
+    for (int step = kThreads / 2; step > 0; step >>= 1)
+        if (bc.rpre[owner + step] <= rr) owner += step;
+    return owner;
+}
+
+// The reached tiles [L, R] of row rr (< total_rows) of the block, and its tile row.
+__device__ __forceinline__ int2 block_row_span(const BlockCoverRows& bc, int owner, uint32_t rr, int& ty) {
+    const uint4 rc = bc.rect[owner];
+    ty = (int)rc.y + (int)(rr - bc.rpre[owner]);
+    const Cover& v = bc.cv[owner];
+    return row_span(v, reach_of(v), ty, (int)rc.x, (int)(rc.x + rc.z) - 1);
+}
+
+// Inclusive sum of v over this lane's run of equal owners (runs are consecutive lanes, owners
+// non-decreasing across the warp), and whether the lane ends its run.
+__device__ __forceinline__ uint32_t run_inclusive_sum(uint32_t v, int owner, bool active, bool& run_end) {
+    const int lane = threadIdx.x & 31;
+    const int key = active ? owner : -1 - lane;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+        const int o = __shfl_up_sync(0xffffffffu, key, d);
+        if (lane >= d && o == key) v += y;
+    }
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    run_end = active && (lane == 31 || next != key);
+    return v;
+}
+
+// Count pass of the wide Gaussians, row by row: each thread takes one row of a round, and the rows
+// of a Gaussian in a warp add their reached tiles with one atomic.  Out of line, so that the tile
+// path of the calling kernel keeps its own register allocation.
+__device__ __noinline__ void count_rows(const BlockCoverRows& bc, uint32_t* s_cnt) {
+    const uint32_t total_rows = bc.total_rows;
+    for (uint32_t r0 = 0; r0 < total_rows; r0 += kThreads) {   // no barrier: rounds are independent
+        const uint32_t rr = r0 + threadIdx.x;
+        const bool active = rr < total_rows;
+        int owner = 0;
+        uint32_t n = 0;
+        if (active) {
+            owner = row_owner(bc, rr);
+            int ty;
+            const int2 sp = block_row_span(bc, owner, rr, ty);
+            n = sp.y >= sp.x ? (uint32_t)(sp.y - sp.x + 1) : 0u;
+        }
+        bool run_end;
+        const uint32_t run = run_inclusive_sum(n, owner, active, run_end);
+        if (run_end && run) atomicAdd(&s_cnt[owner], run);
+    }
+}
+
+// Duplication pass of the wide Gaussians, row by row, in rounds of kThreads rows: each warp run of a
+// Gaussian's rows claims one slice of the Gaussian's range, then the round's splats are dealt out
+// over the threads, kThreads per step, each finding its row by a binary search over the round's
+// prefix.  Out of line, so that the tile path of the calling kernel keeps its own register
+// allocation.
+__device__ __noinline__ void duplicate_rows(const BlockCoverRows& bc, const uint32_t* s_off, uint32_t* s_used,
+                                            const uint32_t* s_g, uint32_t grid_w, uint32_t* __restrict__ tile_keys,
+                                            uint32_t* __restrict__ vals, uint32_t n_total) {
+    __shared__ uint32_t s_rpre[kThreads], s_rpos[kThreads], s_rtile[kThreads], s_rg[kThreads];
+    __shared__ uint32_t s_rws[kWarps];
+    const uint32_t total_rows = bc.total_rows;
+    for (uint32_t r0 = 0; r0 < total_rows; r0 += kThreads) {
+        const uint32_t rr = r0 + threadIdx.x;
+        const bool active = rr < total_rows;
+        int owner = 0;
+        uint32_t n = 0, tile0 = 0;
+        if (active) {
+            owner = row_owner(bc, rr);
+            int ty;
+            const int2 sp = block_row_span(bc, owner, rr, ty);
+            if (sp.y >= sp.x) {
+                n = (uint32_t)(sp.y - sp.x + 1);
+                tile0 = (uint32_t)ty * grid_w + (uint32_t)sp.x;
+            }
+        }
+        // the run of rows of one Gaussian in this warp claims one slice; each row takes its part
+        bool run_end;
+        const uint32_t incl = run_inclusive_sum(n, owner, active, run_end);
+        uint32_t base = 0;
+        if (run_end && incl) base = atomicAdd(&s_used[owner], incl);
+        const uint32_t ends = __ballot_sync(0xffffffffu, run_end);
+        const int lane = threadIdx.x & 31;
+        const uint32_t mine = ends & ~((1u << lane) - 1u);   // this lane's run ends at or above it
+        base = __shfl_sync(0xffffffffu, base, mine ? __ffs(mine) - 1 : 31);
+        uint32_t round_total;
+        const uint32_t pre = block_exclusive_scan<uint32_t, kThreads>(n, s_rws, round_total);
+        s_rpre[threadIdx.x] = active ? pre : round_total;
+        s_rpos[threadIdx.x] = s_off[owner] + base + (incl - n);
+        s_rtile[threadIdx.x] = tile0;
+        s_rg[threadIdx.x] = s_g[owner];
+        __syncthreads();
+        for (uint32_t s0 = 0; s0 < round_total; s0 += kThreads) {
+            const uint32_t idx = s0 + threadIdx.x;
+            if (idx < round_total) {
+                int row = 0;
+#pragma unroll
+                for (int step = kThreads / 2; step > 0; step >>= 1)
+                    if (s_rpre[row + step] <= idx) row += step;
+                const uint32_t k = idx - s_rpre[row];
+                const uint32_t pos = s_rpos[row] + k;
+                if (pos < n_total) {   // always below N: the counts came from the same rows
+                    tile_keys[pos] = s_rtile[row] + k;
+                    vals[pos] = s_rg[row];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Depth keys, per-Gaussian splat counts, range clearing and the digit totals of pass 0.  The count
 // is the rectangle's tile count, or with EXACT the number of its tiles that pass the coverage test
-// (added up per Gaussian in shared memory, one atomic per warp run).
-template <bool EXACT>
-__global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, const float* __restrict__ mean2d,
+// (added up per Gaussian in shared memory, one atomic per warp run): tile by tile, or with ROWS
+// tile by tile for the narrow Gaussians and by rows for the wide ones.
+template <bool EXACT, bool ROWS>
+__global__ void __launch_bounds__(kThreads, kCoverBlocksPerSm) k_bin_keys(DevCamera cam, int P, const float* __restrict__ mean2d,
                                                        const int32_t* __restrict__ radius,
                                                        const float* __restrict__ depth,
                                                        const float* __restrict__ conic,
@@ -385,15 +655,17 @@ __global__ void __launch_bounds__(kThreads) k_bin_keys(DevCamera cam, int P, con
         vals[i] = (uint32_t)i;
         return;
     }
-    __shared__ BlockCover s_bc;
+    __shared__ typename std::conditional<ROWS, BlockCoverRows, BlockCover>::type s_bc;
     __shared__ uint32_t s_cnt[kThreads];
     if ((int)(blockIdx.x * blockDim.x) >= P) return;   // the whole block is past the end
     s_cnt[threadIdx.x] = 0u;
-    stage_block_cover(s_bc, cam, i < P, (uint32_t)i, mean2d, radius, conic, opacity);   // ends with a barrier
+    if constexpr (ROWS) stage_block_exact(s_bc, cam, i < P, (uint32_t)i, mean2d, radius, conic, opacity);
+    else stage_block_cover(s_bc, cam, i < P, (uint32_t)i, mean2d, radius, conic, opacity);   // both end with a barrier
     block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool, bool, int owner, uint32_t, bool leader, uint32_t cnt,
                                                       uint32_t, int) {
         if (leader && cnt) atomicAdd(&s_cnt[owner], cnt);
     });
+    if constexpr (ROWS) count_rows(s_bc, s_cnt);   // the wide Gaussians, row by row
     __syncthreads();
     if (i < P) {
         const uint32_t c = s_cnt[threadIdx.x];
@@ -466,10 +738,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_final(const uint32_t* __restr
 // occupy one contiguous output range, which the block writes cooperatively, 256 splats per round
 // (thread t takes splat t of the round, its Gaussian found by a binary search over the block's
 // prefix of rectangle sizes).  Writes are coalesced and a Gaussian with thousands of tiles is spread
-// over the whole block.  With EXACT, only the tiles that pass the coverage test are written, packed
-// by a block scan in the same order (the block's range then holds exactly the counted splats).
-template <bool EXACT>
-__global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t P, const uint32_t* __restrict__ order,
+// over the whole block.  With EXACT, only the tiles that pass the coverage test are written: those
+// of narrow Gaussians tile by tile as above, those of wide ones from their rows' reached intervals
+// (the block's range then holds exactly the counted splats).
+template <bool EXACT, bool ROWS>
+__global__ void __launch_bounds__(kThreads, kCoverBlocksPerSm) k_duplicate(DevCamera cam, uint32_t P, const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint32_t* __restrict__ counts,
                                                         const float* __restrict__ mean2d,
@@ -479,7 +752,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
                                                         uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ n_u32) {
     pdl_wait();
-    __shared__ BlockCover s_bc;
+    __shared__ typename std::conditional<ROWS, BlockCoverRows, BlockCover>::type s_bc;
     __shared__ uint32_t s_g[kThreads];
     __shared__ uint32_t s_off[kThreads], s_used[kThreads];
     __shared__ uint32_t s_first;
@@ -498,12 +771,14 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
     if (threadIdx.x == 0) s_first = off;
     s_g[threadIdx.x] = g;
     if (EXACT) {
-        // a Gaussian's passing tiles fill its own range [offset, offset + count) in any order (the
-        // stable tile passes keep only the order between Gaussians); each warp run claims a slice
-        // of it with one shared-memory atomic
+        // A Gaussian's splats fill its own range [offset, offset + count) in any order (the stable
+        // tile passes keep only the order between Gaussians): every piece of work claims a slice of
+        // it with a shared-memory atomic.
         s_off[threadIdx.x] = off;
         s_used[threadIdx.x] = 0u;
-        stage_block_cover(s_bc, cam, listed, g, mean2d, radius, conic, opacity);   // ends with a barrier
+        if constexpr (ROWS) stage_block_exact(s_bc, cam, listed, g, mean2d, radius, conic, opacity);
+        else stage_block_cover(s_bc, cam, listed, g, mean2d, radius, conic, opacity);   // both end with a barrier
+        // tile by tile: each warp run of a Gaussian claims a slice of its range
         block_cover_splats(s_bc, (uint32_t)cam.grid_w, [&](bool pass, bool, int owner, uint32_t tile, bool leader,
                                                           uint32_t cnt, uint32_t rank, int first) {
             uint32_t base = 0;
@@ -515,6 +790,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(DevCamera cam, uint32_t 
                 vals[pos] = s_g[owner];
             }
         });
+        if constexpr (ROWS) duplicate_rows(s_bc, s_off, s_used, s_g, (uint32_t)cam.grid_w, tile_keys, vals, n_total);
         return;
     }
     // every rectangle tile is a splat: the block's splats fill [first, first + total) in order
@@ -678,11 +954,17 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     int n_init = P > 2 * num_tiles ? P : 2 * num_tiles;
     if (n_init < kThreads) n_init = kThreads;
     const int kb_blocks = (n_init + kThreads - 1) / kThreads;
-    if (exact)
-        launch_pdl(k_bin_keys<true>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
+    // the row path pays off for wide footprints: chosen when the caller's capacity allows at least
+    // kRowsCapacityPerGaussian splats per Gaussian (the lists are the same either way)
+    const bool rows = exact && splat_capacity >= (int64_t)kRowsCapacityPerGaussian * P;
+    if (rows)
+        launch_pdl(k_bin_keys<true, true>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
+                   w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
+    else if (exact)
+        launch_pdl(k_bin_keys<true, false>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
                    w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
     else
-        launch_pdl(k_bin_keys<false>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
+        launch_pdl(k_bin_keys<false, false>, kb_blocks, kThreads, 0, s, dc, P, mean2d, radius, depth, conic, opacity, w.dk_a,
                    w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
@@ -724,11 +1006,14 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     uint32_t* vbuf[2] = {ids_sorted, w.sv_b};
     int src = (tpasses & 1) ? 1 : 0;
     const int dup_blocks = (P + kThreads - 1) / kThreads;
-    if (exact)
-        launch_pdl(k_duplicate<true>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
-                   radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
+    if (rows)
+        launch_pdl(k_duplicate<true, true>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts,
+                   mean2d, radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
+    else if (exact)
+        launch_pdl(k_duplicate<true, false>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts,
+                   mean2d, radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
     else
-        launch_pdl(k_duplicate<false>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
+        launch_pdl(k_duplicate<false, false>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts, mean2d,
                    radius, conic, opacity, kbuf[src], vbuf[src], w.n_u32);
     count_launches(1);
     TCGS_CHECK_LAUNCH();

@@ -203,17 +203,29 @@ def _borderline(cam, inp, g, t, rel=1e-4, absol=2e-3):
     return abs(qmin - lim) <= rel * (abs(lim) + qmin) + absol
 
 
-@pytest.mark.parametrize("name,make", SMALL + [("diff_crop_320x180", lambda: scenes.differentiation(
-    P=20_000, width=320, height=180, seed=13)[:2])])
-def test_bin_sort_exact_matches_oracle(tc, name, make):
-    """Exact tile coverage: per tile, the GPU list equals the oracle's on the same FP32 inputs except
-    for splats whose decision lies within FP32 rounding of the limit (each checked, and rare)."""
+EXACT_SCENES = SMALL + [("diff_crop_320x180", lambda: scenes.differentiation(P=20_000, width=320, height=180,
+                                                                              seed=13)[:2]),
+                        ("large_crop_960x540", lambda: scenes.large(P=20_000, width=960, height=540, seed=14))]
+
+
+def _capacity(n_rect, P, rows):
+    """A capacity of at least 32 splats per Gaussian selects the row path of exact coverage."""
+    return max(n_rect + 5, 32 * P + 5) if rows else n_rect + 5
+
+
+@pytest.mark.parametrize("rows", [False, True])
+@pytest.mark.parametrize("name,make", EXACT_SCENES)
+def test_bin_sort_exact_matches_oracle(tc, name, make, rows):
+    """Exact tile coverage, tile by tile or (rows) by rows for the wide Gaussians: per tile, the GPU
+    list equals the oracle's on the same FP32 inputs except for splats whose decision lies within
+    FP32 rounding of the limit (each checked, and rare)."""
     cam, sc = make()
     _, inp, b_rect, _ = oracle_frame(cam, sc, render=False)
     b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"], conic=inp["conic"],
                         opacity=inp["opacity"])
     g = gpu_inputs(inp, b)
-    out = tc.tcgs_bin_sort(cam, g["mean2d"], g["radius"], g["depth"], capacity=b_rect["n"] + 5, conic=g["conic"],
+    out = tc.tcgs_bin_sort(cam, g["mean2d"], g["radius"], g["depth"],
+                           capacity=_capacity(b_rect["n"], len(inp["opacity"]), rows), conic=g["conic"],
                            opacity=g["opacity"])
     torch.cuda.synchronize()
     assert int(out["status"].item()) == 0
@@ -229,7 +241,7 @@ def test_bin_sort_exact_matches_oracle(tc, name, make):
         assert all(_borderline(cam, inp, gg, t) for gg in diff), (name, t, diff)
         keep = lambda l: [x for x in l if x not in diff]
         assert keep(lo) == keep(lg), (name, t)
-    print(f"\n[exact bins] {name}: {n} splats (3-sigma: {b_rect['n']}), {mism} borderline differences")
+    print(f"\n[exact bins] {name} rows={rows}: {n} splats (3-sigma: {b_rect['n']}), {mism} borderline differences")
     assert mism <= max(2, 1e-4 * b["n"])
     assert n < b_rect["n"]
 
@@ -269,8 +281,10 @@ def test_exact_tiles_render_the_same_image(tc, precision):
     print(f"\n[exact tiles] {precision}: splats {r['n']} -> {e['n']}")
 
 
-def test_bin_sort_exact_long_lists_and_ties(tc):
-    """Exact coverage on tiles with thousands of candidate splats and exact depth ties."""
+@pytest.mark.parametrize("rows", [False, True])
+def test_bin_sort_exact_long_lists_and_ties(tc, rows):
+    """Exact coverage on tiles with thousands of candidate splats and exact depth ties, tile by tile
+    or by rows for the wide Gaussians."""
     cam = scenes.pinhole(100, 70, fx=100.0)
     rng = np.random.default_rng(23)
     P = 20_000
@@ -284,7 +298,8 @@ def test_bin_sort_exact_long_lists_and_ties(tc):
     depth = f32(rng.choice([1.0, 2.0, 3.0, 4.0], P))
     inp = dict(mean2d=mean2d, conic=conic, opacity=opacity)
     b = oracle.bin_sort(cam, mean2d, radius, depth, conic=conic, opacity=opacity)
-    out = tc.tcgs_bin_sort(cam, to_torch(mean2d, DEV), to_torch(radius, DEV), to_torch(depth, DEV), capacity=b["n"] + 64,
+    out = tc.tcgs_bin_sort(cam, to_torch(mean2d, DEV), to_torch(radius, DEV), to_torch(depth, DEV),
+                           capacity=max(b["n"] + 64, 32 * P + 64) if rows else b["n"] + 64,
                            conic=to_torch(conic, DEV), opacity=to_torch(opacity, DEV))
     torch.cuda.synchronize()
     n = int(out["n_splats"].item())
@@ -296,6 +311,28 @@ def test_bin_sort_exact_long_lists_and_ties(tc):
             diff = set(lo) ^ set(lg)
             assert all(_borderline(cam, inp, gg, t) for gg in diff), (t, diff)
             assert [x for x in lo if x not in diff] == [x for x in lg if x not in diff]
+
+
+@pytest.mark.parametrize("name,make", EXACT_SCENES[-2:])
+def test_bin_sort_exact_rows_equal_tiles(tc, name, make):
+    """The row path of exact coverage (wide Gaussians: each row's reached tiles from the ellipse's
+    shadow, the end tiles settled by the per-tile test) makes the lists of the tile-by-tile path."""
+    cam, sc = make()
+    dsc = {k: to_torch(v, DEV) if isinstance(v, np.ndarray) else v for k, v in sc.items()}
+    pr = tc.tcgs_project(cam, dsc["means3"], dsc["scales"], dsc["quats"], dsc["sh"], sc["sh_degree"])
+    n_rect = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    P = len(sc["opacity"])
+    res = []
+    for rows in (False, True):
+        b = tc.tcgs_bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"], _capacity(n_rect, P, rows),
+                             conic=pr["conic"], opacity=dsc["opacity"])
+        torch.cuda.synchronize()
+        n = int(b["n_splats"].item())
+        res.append((n, b["ids_sorted"][:n].cpu().numpy(), b["tile_ranges"].cpu().numpy()))
+    assert res[0][0] == res[1][0] and res[0][0] > 0
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    np.testing.assert_array_equal(res[0][2], res[1][2])
+    print(f"\n[rows = tiles] {name}: {res[0][0]} splats of {n_rect} rectangle tiles")
 
 
 def test_frame_pipeline_matches_direct_frames(tc):
