@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the differentiation, scheduler and large workloads (reported beside the headline)")
     ap.add_argument("--sched-train-views", type=int, default=200)
+    ap.add_argument("--large-frames", type=int, default=0, metavar="P",
+                    help="profiling run: two frames of the large workload's distribution with P Gaussians, "
+                         "stage times per frame (no headline line)")
     ap.add_argument("--coverage", default="exact", choices=["exact", "square"],
                     help="tile coverage of the headline binning: the 3-sigma square of the paper's pipeline, or "
                          "exact (tcgs_bin_sort_exact); the other one is timed beside it")
@@ -772,10 +775,40 @@ def run_tcgs(args):
         dist.destroy_process_group()
 
 
+def run_large_frames(args):
+    """Two frames (project, bin_sort, TC render, FP32 render) of the 3840x2160 large-workload
+    distribution with args.large_frames Gaussians: the small case for ncu captures of that workload."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    from paper_2505_24796_gb300 import scenes
+    cam, sc = scenes.large(P=args.large_frames)
+    d = tc.scene_to_device(sc, "cuda")
+    pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    del pr
+    r = tc.Renderer(cam, len(sc["opacity"]), n + 1024, device="cuda")
+    steps = [("project", lambda: r.project(d)), ("bin_sort", lambda: r.bin_sort()),
+             ("render_tc", lambda: r.render(d["opacity"], "tc_fp16_split")),
+             ("render_fp32", lambda: r.render(d["opacity"], "fp32"))]
+    for frame in range(2):
+        ms = {}
+        for name, fn in steps:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms[name] = e0.elapsed_time(e1)
+        print(json.dumps({"large_frames": args.large_frames, "frame": frame, "rect_tiles": n,
+                          "splats": int(r.bins["n_splats"].item()), "ms": ms}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.large_frames > 0:
+        run_large_frames(args)
     else:
         run_tcgs(args)
 
