@@ -531,6 +531,32 @@ def bench_tight_radius(cam, sc, dsc, dev, flush, with_oracle=True, reps=20, warm
     return out
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the default process group (x itself without one): the step
+    time of the slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ms_slowest: float, world: int) -> float:
+    """Whole-job frames/s: every replica renders one frame per step, so world frames per step of
+    the slowest replica."""
+    return world * 1000.0 / ms_slowest
+
+
+def barrier_if_distributed():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_tcgs(args):
@@ -580,26 +606,23 @@ def run_tcgs(args):
     use_graph = not args.no_graph
     # --- FP32 comparison path
     tot32, st32 = time_frames(r, dsc, "fp32", args.steps, args.warmup, use_graph, flush, stream)
-    # --- headline path, with clocks sampled during the timed region
-    if world > 1:
-        dist.barrier()
+    # --- headline path, with clocks sampled during the timed region; a barrier and a device
+    # synchronisation on both sides of it
+    barrier_if_distributed()
     torch.cuda.synchronize()
     l0 = lib.tcgs_kernel_launches()
     with ClockSampler(local) as clk:
         tot, stg = time_frames(r, dsc, args.precision, args.steps, args.warmup, use_graph, flush, stream)
     launches_total = lib.tcgs_kernel_launches() - l0
     torch.cuda.synchronize()
+    barrier_if_distributed()
     # launches per frame, counted by the library on one eager frame (graphs replay the same kernels)
     l1 = lib.tcgs_kernel_launches()
     r.frame(dsc, precision=args.precision)
     torch.cuda.synchronize()
     launches_per_frame = lib.tcgs_kernel_launches() - l1
-    ms = statistics.mean(tot)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    fps = world * 1000.0 / ms
+    ms = max_over_ranks(statistics.mean(tot), dev)
+    fps = job_rate(ms, world)
     ms32 = statistics.mean(tot32)
     render_ms = statistics.mean(stg[2])
     render32_ms = statistics.mean(st32[2])
@@ -628,7 +651,7 @@ def run_tcgs(args):
     e1.synchronize()
     e2e_ms = [e0.elapsed_time(e1) / args.steps]
     e2e_img_ok = bool(torch.equal(host_imgs[(args.steps - 1) & 1], img_tc.cpu()))
-    e2e_fps = world * 1000.0 / statistics.mean(e2e_ms)
+    e2e_fps = job_rate(max_over_ranks(statistics.mean(e2e_ms), dev), world)
 
     if world > 1:
         dist.barrier()
