@@ -382,6 +382,14 @@ TCGS_API tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam /* host */, int32
                                const float* opacity, int32_t n_tiles, const int32_t* tiles, int32_t max_n,
                                float* beta_out, int32_t* device_status, tcgs_stream stream);
 
+/*
+ * Self-test of the device-side failure reporting: one kernel waits, with the bounded mbarrier wait
+ * that the tensor-core renderer uses, on a barrier that nothing completes.  After `polls` polls
+ * (1 .. 2^22; the renderer uses 2^22) the wait gives up and TCGS_ERR_TIMEOUT is written to
+ * device_status (device int32, first error wins); the context stays usable.
+ */
+TCGS_API tcgs_status tcgs_selftest_bounded_wait(int32_t* device_status, uint32_t polls, tcgs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ SIGNATURES = {
     "tcgs_sched_order_workspace_size": (c_size_t, [c_int32]),
     "tcgs_sched_order": (c_int32, [V, V, c_int32, V, V, c_size_t, V]),
     "tcgs_frag2mat_beta": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int32, V, c_int32, V, V, V]),
+    "tcgs_selftest_bounded_wait": (c_int32, [V, ctypes.c_uint32, V]),
 }
 
 _lock = threading.Lock()

@@ -98,8 +98,8 @@ __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint32_t polls = 1u << 22) {
+    for (uint32_t i = 0; i < polls; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -664,6 +664,16 @@ void zero_counter(uint32_t* c, cudaStream_t s) {
     count_launches(1);
 }
 
+// The renderer's bounded mbarrier wait on a barrier that nothing completes: it must give up after
+// `polls` polls and report TCGS_ERR_TIMEOUT, leaving the context usable.
+__global__ void k_wait_selftest(int32_t* status, uint32_t polls) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t a = smem_u32(&bar);
+    if (threadIdx.x == 0) mbar_init(a, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(a, 0u, polls)) set_status(status, TCGS_ERR_TIMEOUT);
+}
+
 int g_checked_device = -1;
 bool g_device_ok = false;
 int g_sm_count = 0;
@@ -880,4 +890,14 @@ extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precis
     p.status = device_status;
     p.dbg_tiles = tiles; p.dbg_max_n = max_n; p.dbg_beta = beta_out;
     return launch_tc<true, false, false>(p, n_tiles, (cudaStream_t)stream);
+}
+
+extern "C" tcgs_status tcgs_selftest_bounded_wait(int32_t* device_status, uint32_t polls, tcgs_stream stream) {
+    using namespace tcgs;
+    if (!device_status || polls == 0 || polls > (1u << 22)) return TCGS_ERR_INVALID;
+    if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(device_status, polls);
+    count_launches(1);
+    TCGS_CHECK_LAUNCH();
+    return TCGS_OK;
 }

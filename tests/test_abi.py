@@ -71,6 +71,8 @@ def test_invalid_arguments_rejected_on_host(lib):
         _lib.TCGS_ERR_INVALID
     assert lib.tcgs_bin_sort_exact(ctypes.byref(cam), 10, V, V, V, V, V, 100, V, 0, V, V, V, V, None) == \
         _lib.TCGS_ERR_INVALID   # conic and opacity required
+    assert lib.tcgs_selftest_bounded_wait(V, 16, None) == _lib.TCGS_ERR_INVALID          # no status word
+    assert lib.tcgs_selftest_bounded_wait(ctypes.c_void_p(256), 0, None) == _lib.TCGS_ERR_INVALID   # no polls
 
 
 def test_build_targets_sm103a_only():

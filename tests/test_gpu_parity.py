@@ -417,6 +417,25 @@ def test_tile_order_is_the_stable_longest_first_sort(tc, width, height):
     np.testing.assert_array_equal(got, np.argsort(-groups, kind="stable"))
 
 
+def test_bounded_wait_reports_timeout_and_context_stays_usable(tc):
+    """A device-side wait that nothing ends gives up after its poll limit and reports
+    TCGS_ERR_TIMEOUT in the status word; the next launches run normally."""
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    for polls in (1, 4096):
+        status.zero_()
+        tc.tcgs_selftest_bounded_wait(status, polls)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 4   # TCGS_ERR_TIMEOUT
+    cam, sc = SMALL[0][1]()
+    _, inp, b, o = oracle_frame(cam, sc)
+    g = gpu_inputs(inp, b)
+    out = tc.tcgs_render_fwd(cam, tc.render_opts("tc_fp16_split", device_status=status.zero_()), g["ranges"],
+                             g["ids"], g["mean2d"], g["conic"], g["opacity"], g["rgb"])
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert psnr(out["img"].cpu().numpy(), o["img"]) > 50
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
