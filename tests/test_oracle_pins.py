@@ -307,6 +307,26 @@ def test_exact_coverage_drops_only_splats_culled_at_every_pixel(seed):
             assert qmin <= 2 * (math.log(op[g]) + math.log(255.0)) * 1.0001 + 1e-3
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_exact_coverage_rows_are_runs(seed):
+    """In every row of tiles, the tiles a Gaussian's exact list entries fall in form one run of
+    consecutive tiles: the reach region {q <= L} is convex and each tile's pixel-centre box spans the
+    same band of rows, so a box meets the region exactly when its x-range meets the region's shadow
+    on the band (an interval).  This is what lets wide Gaussians be covered row by row."""
+    cam, sc, pr, op, rect, exact = _exact_case(seed, P=600, width=256, height=160)
+    gw, gh = oracle.grid(cam)
+    rows = {}
+    for t, lst in enumerate(_tile_lists(exact)):
+        for g in lst:
+            rows.setdefault((g, t // gw), []).append(t % gw)
+    wide = 0
+    for (g, ty), txs in rows.items():
+        txs = sorted(txs)
+        assert txs == list(range(txs[0], txs[-1] + 1)), (g, ty, txs)
+        wide += len(txs) >= 3
+    assert wide > 20   # the scenes have Gaussians several tiles wide
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_exact_coverage_renders_the_same_image(seed):
     """Algorithm 1 over the exact lists gives the image and final transmittance of the 3-sigma
