@@ -666,7 +666,7 @@ def run_tcgs(args):
     mse_tc_fp32 = float(np.mean((img_tc_np - img32_np) ** 2))
     cpu_baseline = None
     acc = {"psnr_tc_vs_fp32_db": (10 * math.log10(1 / mse_tc_fp32) if mse_tc_fp32 > 0 else None)}
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # the host-core baseline is taken at N = 1 only
         est, info = oracle_frame_estimate(cam, sc, 1.0, seed=1)   # the whole frame
         est2, info2 = oracle_frame_estimate(cam, sc, 1.0, seed=2)
         est = 0.5 * (est + est2)
