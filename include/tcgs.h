@@ -199,6 +199,10 @@ TCGS_API tcgs_status tcgs_bin_sort(const tcgs_camera* cam /* host */, int32_t P,
  * that hold for the FP32 and tensor-core renderers' own arithmetic too, so every image rendered from
  * these lists equals the image rendered from tcgs_bin_sort's (only list positions, and so
  * n_contrib, differ).  Order, ranges, outputs, workspace and status as tcgs_bin_sort.
+ * When splat_capacity >= 32 P (wide footprints), Gaussians whose rectangle is at least 6 tiles wide
+ * are covered row by row: in a tile row the reached tiles form one run (the region q <= L is
+ * convex), found from the ellipse's extent with its end tiles settled by the test above, so the
+ * lists are the same; this needs Q positive definite, as tcgs_project makes it.
  * In:  conic [P,3], opacity [P] (post-sigmoid) as given to the renderer; both non-null when P > 0.
  */
 TCGS_API tcgs_status tcgs_bin_sort_exact(const tcgs_camera* cam /* host */, int32_t P, const float* mean2d,
