@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--large-frames", type=int, default=0, metavar="P",
                     help="profiling run: two frames of the large workload's distribution with P Gaussians, "
                          "stage times per frame (no headline line)")
+    ap.add_argument("--diff-frames", action="store_true",
+                    help="profiling run: two forward + backward frames of the differentiation workload, stage "
+                         "times per frame (no headline line)")
     ap.add_argument("--coverage", default="exact", choices=["exact", "square"],
                     help="tile coverage of the headline binning: the 3-sigma square of the paper's pipeline, or "
                          "exact (tcgs_bin_sort_exact); the other one is timed beside it")
@@ -826,12 +829,60 @@ def run_large_frames(args):
                           "splats": int(r.bins["n_splats"].item()), "ms": ms}), flush=True)
 
 
+def run_diff_frames(args):
+    """Two frames of the differentiation workload (1280x720, 500k Gaussians): project, bin_sort, FP32
+    render, render backward (L1 loss to the seeded target), projection backward: the small case for
+    ncu captures of the backward."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    from paper_2505_24796_gb300 import scenes
+    cam, sc, target = scenes.differentiation()
+    d = tc.scene_to_device(sc, "cuda")
+    pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    del pr
+    P = len(sc["opacity"])
+    r = tc.Renderer(cam, P, n + 1024, device="cuda")
+    tgt = torch.from_numpy(target).to("cuda")
+    grads = dict(dmean2d=torch.zeros(P, 2, device="cuda"), dconic=torch.zeros(P, 3, device="cuda"),
+                 dopacity=torch.zeros(P, device="cuda"), drgb=torch.zeros(P, 3, device="cuda"))
+    g3 = dict(dmeans3=torch.zeros_like(d["means3"]), dscales=torch.zeros_like(d["scales"]),
+              dquats=torch.zeros_like(d["quats"]), dsh=torch.zeros_like(d["sh"]))
+    opts = tc.render_opts("fp32")
+    gimg = {}
+
+    def render_bwd():
+        gimg["g"] = torch.sign(r.out["img"] - tgt).contiguous()
+        tc.tcgs_render_bwd(r.cam, opts, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"],
+                           r.proj["conic"], d["opacity"], r.proj["rgb"], r.out["img"], r.out["T_final"],
+                           r.out["n_contrib"], gimg["g"], grads=grads)
+
+    steps = [("project", lambda: r.project(d)), ("bin_sort", lambda: r.bin_sort()),
+             ("render_fp32", lambda: r.render(d["opacity"], "fp32")), ("render_bwd", render_bwd),
+             ("project_bwd", lambda: tc.tcgs_project_bwd(r.cam, d["means3"], d["scales"], d["quats"], d["sh"],
+                                                         d["sh_degree"], r.proj["radius"], grads["dmean2d"],
+                                                         grads["dconic"], grads["drgb"], grads=g3))]
+    for frame in range(2):
+        ms = {}
+        for name, fn in steps:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms[name] = e0.elapsed_time(e1)
+        print(json.dumps({"diff_frames": P, "frame": frame, "splats": int(r.bins["n_splats"].item()), "ms": ms}),
+              flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.large_frames > 0:
         run_large_frames(args)
+    elif args.diff_frames:
+        run_diff_frames(args)
     else:
         run_tcgs(args)
 
