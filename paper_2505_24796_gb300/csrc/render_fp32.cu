@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_fp32(FwdParams p) {
 
 // ---------------------------------------------------------------- backward
 //
-// One CTA per tile, one thread per pixel; each warp owns an 8 x 4 pixel block.  Each pixel replays
+// One CTA of 128 threads per tile, two pixels a thread; each warp owns an 8 x 8 pixel block.  Each pixel replays
 // its fragments 0 .. n_contrib-1 front to back with the forward's FP32 alpha arithmetic, so T_j
 // matches the forward bit for bit; the colour blended after fragment j is img - bg T_final -
 // (prefix up to j).  A warp replays only the fragments that can reach alpha >= 1/255 somewhere in
@@ -184,18 +184,23 @@ __device__ __forceinline__ void warp_sum9_store(const float (&v)[9], float* part
 
 // Gradient partial sums of a fragment: each warp parks its 9 sums in shared memory (slots of
 // fragments it does not replay, or to which none of its pixels contributes, stay zero); every
-// kBwdChunk fragments the block adds the 8 warps' sums, clears the slots, and issues one global
-// atomic per nonzero (fragment, parameter) -- 8 times fewer same-address atomics than one per warp.
+// kBwdChunk fragments the block adds the warps' sums, clears the slots, and issues one global atomic
+// per nonzero (fragment, parameter).
 constexpr int kBwdChunk = 32;
-constexpr int kBwdWarps = kFwdThreads / 32;
+constexpr int kBwdThreads = 128;               // 4 warps of 8 x 8 pixels, two pixels a thread
+constexpr int kBwdWarps = kBwdThreads / 32;
+constexpr int kBwdBatch = 256;                 // fragments staged in shared memory at a time
 constexpr int kBwdParams = 9;   // dmean2d (2), dconic (3), dopacity, drgb (3)
 
-__global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
-    __shared__ float2 s_xy[kFwdThreads];
-    __shared__ float4 s_co[kFwdThreads];   // sigma11, sigma12, sigma22, opacity
-    __shared__ float4 s_rgb[kFwdThreads];  // r, g, b, reach limit
-    __shared__ float4 s_inv[kFwdThreads];  // 1 / sigma11, 1 / sigma22, ln(opacity)
-    __shared__ uint32_t s_id[kFwdThreads];
+// Lane l of warp w replays pixels (8 (w & 1) + l % 8, 8 (w >> 1) + l / 8) and the one 4 rows below,
+// so that one warp reduction per fragment covers 64 pixels and the fragment's loads and block mark
+// serve both.
+__global__ void __launch_bounds__(kBwdThreads) k_render_bwd(BwdParams p) {
+    __shared__ float2 s_xy[kBwdBatch];
+    __shared__ float4 s_co[kBwdBatch];    // sigma11, sigma12, sigma22, opacity
+    __shared__ float4 s_rgb[kBwdBatch];   // r, g, b, reach limit
+    __shared__ float4 s_inv[kBwdBatch];   // 1 / sigma11, 1 / sigma22, ln(opacity)
+    __shared__ uint32_t s_id[kBwdBatch];
     __shared__ uint32_t s_max;
     __shared__ float s_part[kBwdChunk][kBwdWarps][kBwdParams];
     const int warp = threadIdx.x >> 5;
@@ -203,52 +208,61 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
     const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
     const int t = threadIdx.x, lane = t & 31;
     const int bx = warp & 1, by = warp >> 1;
-    const int lx = 8 * bx + (lane & 7), ly = 4 * by + (lane >> 3);
-    const int px_i = tx * kTile + lx, py_i = ty * kTile + ly;
-    const bool inside = px_i < p.cam.width && py_i < p.cam.height;
-    const float px = px_i + 0.5f, py = py_i + 0.5f;
-    // the warp's pixel-centre rectangle relative to the tile centre
+    const int lx = 8 * bx + (lane & 7);
+    // the warp's 8 x 8 pixel-centre rectangle relative to the tile centre
     const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);
-    const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f, by0 = 4.f * by - 7.5f, by1 = by0 + 3.f;
+    const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f, by0 = 8.f * by - 7.5f, by1 = by0 + 7.f;
     const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
+    const float bg0 = p.bg[0], bg1 = p.bg[1], bg2 = p.bg[2];
 
-    uint32_t nc = 0;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f, Tf = 1.f;
-    if (inside) {
-        size_t pix = (size_t)py_i * p.cam.width + px_i;
-        size_t plane = (size_t)p.cam.width * p.cam.height;
-        nc = p.n_contrib[pix];
-        Tf = p.T_final[pix];
-        g0 = p.dL_dimg[pix]; g1 = p.dL_dimg[plane + pix]; g2 = p.dL_dimg[2 * plane + pix];
-        // colour still to come after the current fragment, initially everything blended
-        R0 = p.img[pix] - Tf * p.bg[0];
-        R1 = p.img[plane + pix] - Tf * p.bg[1];
-        R2 = p.img[2 * plane + pix] - Tf * p.bg[2];
+    // per pixel k: n_contrib, dL/dimg, the colour still to come, T_final, the replayed T
+    float px[2], py[2], g0[2], g1[2], g2[2], R0[2], R1[2], R2[2], Tf[2], T[2];
+    uint32_t nc[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int px_i = tx * kTile + lx, py_i = ty * kTile + 8 * by + (lane >> 3) + 4 * k;
+        px[k] = px_i + 0.5f;
+        py[k] = py_i + 0.5f;
+        nc[k] = 0;
+        g0[k] = g1[k] = g2[k] = R0[k] = R1[k] = R2[k] = 0.f;
+        Tf[k] = T[k] = 1.f;
+        if (px_i < p.cam.width && py_i < p.cam.height) {
+            const size_t pix = (size_t)py_i * p.cam.width + px_i;
+            const size_t plane = (size_t)p.cam.width * p.cam.height;
+            nc[k] = p.n_contrib[pix];
+            Tf[k] = p.T_final[pix];
+            g0[k] = p.dL_dimg[pix]; g1[k] = p.dL_dimg[plane + pix]; g2[k] = p.dL_dimg[2 * plane + pix];
+            // colour still to come after the current fragment, initially everything blended
+            R0[k] = p.img[pix] - Tf[k] * bg0;
+            R1[k] = p.img[plane + pix] - Tf[k] * bg1;
+            R2[k] = p.img[2 * plane + pix] - Tf[k] * bg2;
+        }
     }
-    const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc);
+    const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc[0] > nc[1] ? nc[0] : nc[1]);
     if (t == 0) s_max = 0;
-    for (int q = t; q < kBwdChunk * kBwdWarps * kBwdParams; q += kFwdThreads) (&s_part[0][0][0])[q] = 0.f;
+    for (int q = t; q < kBwdChunk * kBwdWarps * kBwdParams; q += kBwdThreads) (&s_part[0][0][0])[q] = 0.f;
     __syncthreads();
     if (lane == 0) atomicMax(&s_max, warp_nc);
     __syncthreads();
     const uint32_t span = s_max;
-    float T = 1.f;
-    for (uint32_t b0 = 0; b0 < span; b0 += kFwdThreads) {
+    for (uint32_t b0 = 0; b0 < span; b0 += kBwdBatch) {
         __syncthreads();
-        uint32_t idx = start + b0 + t;
-        if (idx < end) {
-            uint32_t g = p.ids[idx];
-            const float o = p.opacity[g];
-            const float a = p.conic[3 * g], c = p.conic[3 * g + 2];
-            s_id[t] = g;
-            s_xy[t] = reinterpret_cast<const float2*>(p.mean2d)[g];
-            s_co[t] = make_float4(a, p.conic[3 * g + 1], c, o);
-            const float lno = __logf(o);
-            s_rgb[t] = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], reach_limit(lno));
-            s_inv[t] = make_float4(__fdividef(1.f, a), __fdividef(1.f, c), lno, 0.f);
+        for (int u = t; u < kBwdBatch; u += kBwdThreads) {
+            const uint32_t idx = start + b0 + (uint32_t)u;
+            if (idx < end) {
+                const uint32_t g = p.ids[idx];
+                const float o = p.opacity[g];
+                const float a = p.conic[3 * g], c = p.conic[3 * g + 2];
+                s_id[u] = g;
+                s_xy[u] = reinterpret_cast<const float2*>(p.mean2d)[g];
+                s_co[u] = make_float4(a, p.conic[3 * g + 1], c, o);
+                const float lno = __logf(o);
+                s_rgb[u] = make_float4(p.rgb[3 * g], p.rgb[3 * g + 1], p.rgb[3 * g + 2], reach_limit(lno));
+                s_inv[u] = make_float4(__fdividef(1.f, a), __fdividef(1.f, c), lno, 0.f);
+            }
         }
         __syncthreads();
-        const uint32_t nb = span - b0 < (uint32_t)kFwdThreads ? span - b0 : (uint32_t)kFwdThreads;
+        const uint32_t nb = span - b0 < (uint32_t)kBwdBatch ? span - b0 : (uint32_t)kBwdBatch;
         for (uint32_t c0 = 0; c0 < nb; c0 += kBwdChunk) {
             // this warp's fragments of the chunk: in some pixel's replay range and able to reach the block
             const uint32_t jl = c0 + (uint32_t)lane;
@@ -265,37 +279,41 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
             while (marks) {
                 const uint32_t j = c0 + (uint32_t)(__ffs(marks) - 1);
                 marks &= marks - 1;
+                const float2 m = s_xy[j];
+                const float4 co = s_co[j];
+                const float4 c = s_rgb[j];
+                const float lno = s_inv[j].z;
                 float v[kBwdParams] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 bool contrib = false;
-                if (b0 + j < nc) {
-                    float2 m = s_xy[j];
-                    float4 co = s_co[j];
-                    float dx = m.x - px, dy = m.y - py;
-                    float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                    float G = expf(power);
-                    float raw = co.w * G;
-                    float alpha = fminf(p.alpha_max, raw);
-                    bool early = p.early_cull && power + s_inv[j].z < kBetaCull;   // same test as the forward
-                    if (!early && alpha >= kCullAlpha) {
-                        contrib = true;
-                        float4 c = s_rgb[j];
-                        float w = alpha * T;
-                        v[6] = w * g0; v[7] = w * g1; v[8] = w * g2;
-                        R0 -= c.x * w; R1 -= c.y * w; R2 -= c.z * w;
-                        float ia = 1.f / (1.f - alpha);
-                        float dL_da = g0 * (c.x * T - (R0 + Tf * p.bg[0]) * ia) +
-                                      g1 * (c.y * T - (R1 + Tf * p.bg[1]) * ia) +
-                                      g2 * (c.z * T - (R2 + Tf * p.bg[2]) * ia);
-                        if (raw <= p.alpha_max) {
-                            float dL_dp = dL_da * alpha;
-                            v[5] = dL_da * G;
-                            v[0] = -dL_dp * (co.x * dx + co.y * dy);
-                            v[1] = -dL_dp * (co.y * dx + co.z * dy);
-                            v[2] = -0.5f * dL_dp * dx * dx;
-                            v[3] = -dL_dp * dx * dy;
-                            v[4] = -0.5f * dL_dp * dy * dy;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (b0 + j < nc[k]) {
+                        const float dx = m.x - px[k], dy = m.y - py[k];
+                        const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+                        const float G = expf(power);
+                        const float raw = co.w * G;
+                        const float alpha = fminf(p.alpha_max, raw);
+                        const bool early = p.early_cull && power + lno < kBetaCull;   // same test as the forward
+                        if (!early && alpha >= kCullAlpha) {
+                            contrib = true;
+                            const float w = alpha * T[k];
+                            v[6] += w * g0[k]; v[7] += w * g1[k]; v[8] += w * g2[k];
+                            R0[k] -= c.x * w; R1[k] -= c.y * w; R2[k] -= c.z * w;
+                            const float ia = __frcp_rn(1.f - alpha);   // = 1 / (1 - alpha), correctly rounded
+                            const float dL_da = g0[k] * (c.x * T[k] - (R0[k] + Tf[k] * bg0) * ia) +
+                                                g1[k] * (c.y * T[k] - (R1[k] + Tf[k] * bg1) * ia) +
+                                                g2[k] * (c.z * T[k] - (R2[k] + Tf[k] * bg2) * ia);
+                            if (raw <= p.alpha_max) {
+                                const float dL_dp = dL_da * alpha;
+                                v[5] += dL_da * G;
+                                v[0] += -dL_dp * (co.x * dx + co.y * dy);
+                                v[1] += -dL_dp * (co.y * dx + co.z * dy);
+                                v[2] += -0.5f * dL_dp * dx * dx;
+                                v[3] += -dL_dp * dx * dy;
+                                v[4] += -0.5f * dL_dp * dy * dy;
+                            }
+                            T[k] = fmaf(-alpha, T[k], T[k]);
                         }
-                        T = fmaf(-alpha, T, T);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) warp_sum9_store(v, s_part[j - c0][warp]);
@@ -303,7 +321,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_render_bwd(BwdParams p) {
             // the block adds the warps' sums of the chunk's fragments: one atomic per value
             __syncthreads();
             const uint32_t nf = nb - c0 < (uint32_t)kBwdChunk ? nb - c0 : (uint32_t)kBwdChunk;
-            for (uint32_t q = threadIdx.x; q < nf * kBwdParams; q += kFwdThreads) {
+            for (uint32_t q = threadIdx.x; q < nf * kBwdParams; q += kBwdThreads) {
                 const uint32_t f = q / kBwdParams, k = q - f * kBwdParams;
                 float sum = 0.f;
 #pragma unroll
@@ -371,7 +389,7 @@ extern "C" tcgs_status tcgs_render_bwd(const tcgs_camera* cam, const tcgs_render
     p.img = img; p.T_final = T_final; p.n_contrib = n_contrib; p.dL_dimg = dL_dimg;
     p.dmean2d = dmean2d; p.dconic = dconic; p.dopacity = dopacity; p.drgb = drgb;
     int tiles = p.cam.grid_w * p.cam.grid_h;
-    k_render_bwd<<<tiles, kFwdThreads, 0, (cudaStream_t)stream>>>(p);
+    k_render_bwd<<<tiles, kBwdThreads, 0, (cudaStream_t)stream>>>(p);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
