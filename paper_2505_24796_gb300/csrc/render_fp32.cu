@@ -187,14 +187,19 @@ __device__ __forceinline__ void warp_sum9_store(const float (&v)[9], float* part
 // kBwdChunk fragments the block adds the warps' sums, clears the slots, and issues one global atomic
 // per nonzero (fragment, parameter).
 constexpr int kBwdChunk = 32;
-constexpr int kBwdThreads = 128;               // 4 warps of 8 x 8 pixels, two pixels a thread
+constexpr int kBwdPix = 2;                     // pixels a thread
+constexpr int kBwdThreads = 256 / kBwdPix;     // one 16 x 16 tile
 constexpr int kBwdWarps = kBwdThreads / 32;
+// a warp's pixel block: 8 x 8 for two pixels a thread (2 x 2 warps), 16 x 8 for four (1 x 2 warps)
+constexpr int kBwdBlockW = kBwdPix == 2 ? 8 : 16, kBwdBlockH = 8;
+static_assert(kBwdPix == 2 || kBwdPix == 4, "two or four pixels a thread");
 constexpr int kBwdBatch = 256;                 // fragments staged in shared memory at a time
 constexpr int kBwdParams = 9;   // dmean2d (2), dconic (3), dopacity, drgb (3)
 
-// Lane l of warp w replays pixels (8 (w & 1) + l % 8, 8 (w >> 1) + l / 8) and the one 4 rows below,
-// so that one warp reduction per fragment covers 64 pixels and the fragment's loads and block mark
-// serve both.
+// Lane l of warp w replays kBwdPix pixels of the warp's block, one column, rows dyk apart (two
+// pixels: (8 (w & 1) + l % 8, 8 (w >> 1) + l / 8) and the one 4 rows below), so that one warp
+// reduction per fragment covers 32 kBwdPix pixels and the fragment's loads and block mark serve all
+// of them.
 __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(BwdParams p) {
     __shared__ float2 s_xy[kBwdBatch];
     __shared__ float4 s_co[kBwdBatch];    // sigma11, sigma12, sigma22, opacity
@@ -207,20 +212,24 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(BwdParams p) {
     const int tile = blockIdx.x;
     const int tx = tile % p.cam.grid_w, ty = tile / p.cam.grid_w;
     const int t = threadIdx.x, lane = t & 31;
-    const int bx = warp & 1, by = warp >> 1;
-    const int lx = 8 * bx + (lane & 7);
-    // the warp's 8 x 8 pixel-centre rectangle relative to the tile centre
+    const int bx = kBwdPix == 2 ? warp & 1 : 0, by = kBwdPix == 2 ? warp >> 1 : warp;
+    const int lx = kBwdBlockW * bx + (lane & (kBwdBlockW - 1));
+    const int ly = kBwdBlockH * by + lane / kBwdBlockW;   // first of the thread's rows; the others follow
+    const int dyk = 32 / kBwdBlockW;                       // rows between a thread's pixels
+    // the warp's pixel-centre rectangle relative to the tile centre
     const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);
-    const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f, by0 = 8.f * by - 7.5f, by1 = by0 + 7.f;
+    const float bx0 = (float)(kBwdBlockW * bx) - 7.5f, bx1 = bx0 + (float)(kBwdBlockW - 1);
+    const float by0 = (float)(kBwdBlockH * by) - 7.5f, by1 = by0 + (float)(kBwdBlockH - 1);
     const uint32_t start = p.ranges[2 * tile], end = p.ranges[2 * tile + 1];
     const float bg0 = p.bg[0], bg1 = p.bg[1], bg2 = p.bg[2];
 
     // per pixel k: n_contrib, dL/dimg, the colour still to come, T_final, the replayed T
-    float px[2], py[2], g0[2], g1[2], g2[2], R0[2], R1[2], R2[2], Tf[2], T[2];
-    uint32_t nc[2];
+    float px[kBwdPix], py[kBwdPix], g0[kBwdPix], g1[kBwdPix], g2[kBwdPix], R0[kBwdPix], R1[kBwdPix],
+        R2[kBwdPix], Tf[kBwdPix], T[kBwdPix];
+    uint32_t nc[kBwdPix];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int px_i = tx * kTile + lx, py_i = ty * kTile + 8 * by + (lane >> 3) + 4 * k;
+    for (int k = 0; k < kBwdPix; ++k) {
+        const int px_i = tx * kTile + lx, py_i = ty * kTile + ly + dyk * k;
         px[k] = px_i + 0.5f;
         py[k] = py_i + 0.5f;
         nc[k] = 0;
@@ -238,7 +247,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(BwdParams p) {
             R2[k] = p.img[2 * plane + pix] - Tf[k] * bg2;
         }
     }
-    const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc[0] > nc[1] ? nc[0] : nc[1]);
+    uint32_t nc_max = 0;
+#pragma unroll
+    for (int k = 0; k < kBwdPix; ++k) nc_max = nc[k] > nc_max ? nc[k] : nc_max;
+    const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc_max);
     if (t == 0) s_max = 0;
     for (int q = t; q < kBwdChunk * kBwdWarps * kBwdParams; q += kBwdThreads) (&s_part[0][0][0])[q] = 0.f;
     __syncthreads();
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(BwdParams p) {
                 float v[kBwdParams] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 bool contrib = false;
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
+                for (int k = 0; k < kBwdPix; ++k) {
                     if (b0 + j < nc[k]) {
                         const float dx = m.x - px[k], dy = m.y - py[k];
                         const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
