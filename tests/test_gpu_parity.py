@@ -436,6 +436,87 @@ def test_bounded_wait_reports_timeout_and_context_stays_usable(tc):
     assert psnr(out["img"].cpu().numpy(), o["img"]) > 50
 
 
+def _tile_mask(cam, tiles):
+    H, W = cam["height"], cam["width"]
+    gw, _ = oracle.grid(cam)
+    m = np.zeros((H, W), bool)
+    for t in tiles:
+        tx, ty = t % gw, t // gw
+        m[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
+    return m
+
+
+def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
+    """The bench's workload (1920x1080, 1M Gaussians, SH3) in the bench's launch configuration (exact
+    tile coverage, persistent TC renderer in longest-list order), checked on 96 random tiles the
+    oracle renders one by one.  (1) On the oracle's FP32-rounded projection: the tile lists match the
+    oracle's (up to splats within FP32 rounding of the coverage limit), the FP32 renderer within 1e-5
+    away from cull and termination margins, the TC renderer at PSNR >= 50 dB with >= 99.9% of pixels
+    within 2e-3.  (2) The whole GPU frame from the scene (GPU projection) against the FP64 oracle
+    frame: the TC criteria again."""
+    cam, sc = scenes.precision()
+    P = len(sc["opacity"])
+    pr, inp, b_rect, _ = oracle_frame(cam, sc, render=False)
+    b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"], conic=inp["conic"], opacity=inp["opacity"])
+    gw, gh = oracle.grid(cam)
+    tiles = np.sort(np.random.default_rng(7).choice(gw * gh, 96, replace=False)).astype(np.int32)
+    o = oracle.render(cam, b, inp["mean2d"], inp["conic"], inp["opacity"], inp["rgb"], tiles=tiles)
+    mask = _tile_mask(cam, tiles)
+
+    # (1) binning and both renderers on the oracle's FP32 inputs
+    g = gpu_inputs(inp, b)
+    out_b = tc.tcgs_bin_sort(cam, g["mean2d"], g["radius"], g["depth"], capacity=b_rect["n"] + 1024,
+                             conic=g["conic"], opacity=g["opacity"])
+    torch.cuda.synchronize()
+    assert int(out_b["status"].item()) == 0
+    n = int(out_b["n_splats"].item())
+    ids, ranges = out_b["ids_sorted"].cpu().numpy()[:n], out_b["tile_ranges"].cpu().numpy()
+    mism = 0
+    for t in tiles:
+        (s0, e0), (s1, e1) = b["ranges"][t], ranges[t]
+        lo, lg = list(b["ids"][s0:e0]), list(ids[s1:e1])
+        if lo != lg:
+            diff = set(lo) ^ set(lg)
+            mism += len(diff)
+            assert all(_borderline(cam, inp, gg, int(t)) for gg in diff), (t, diff)
+            assert [x for x in lo if x not in diff] == [x for x in lg if x not in diff]
+    assert abs(n - b["n"]) <= max(16, 1e-5 * b["n"])
+    order = tc.tcgs_tile_order(cam, out_b["tile_ranges"])
+    counter = torch.zeros(1, dtype=torch.int32, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    imgs = {}
+    for prec in ("fp32", "tc_fp16_split"):
+        opts = tc.render_opts(prec, device_status=status,
+                              tile_order=order if prec != "fp32" else None,
+                              work_counter=counter if prec != "fp32" else None)
+        out = tc.tcgs_render_fwd(cam, opts, out_b["tile_ranges"], out_b["ids_sorted"], g["mean2d"], g["conic"],
+                                 g["opacity"], g["rgb"])
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        imgs[prec] = (out["img"].cpu().numpy(), out["T_final"].cpu().numpy())
+    img32, T32 = imgs["fp32"]
+    keep = mask & ~margin_mask(o, 1e-4, 1e-4)
+    assert keep.sum() > 0.99 * mask.sum()
+    assert np.abs(img32 - o["img"]).max(axis=0)[keep].max() <= 1e-5
+    assert np.abs(T32 - o["T"])[keep].max() <= 1e-5
+    imgtc = imgs["tc_fp16_split"][0]
+    assert psnr(imgtc[:, mask], o["img"][:, mask]) >= 50.0
+    assert (np.abs(imgtc - o["img"]).max(axis=0)[mask] <= 2e-3).mean() >= 0.999
+
+    # (2) the whole frame from the scene, as the bench renders it
+    d = tc.scene_to_device(sc, DEV)
+    r = tc.Renderer(cam, P, b_rect["n"] + 1024, device=DEV)
+    img = r.frame(d)["img"].cpu().numpy()
+    o64 = oracle.render(cam, oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"], conic=pr["conic"],
+                                             opacity=scene64(sc)["opacity"]),
+                        pr["mean2d"], pr["conic"], scene64(sc)["opacity"], pr["rgb"], tiles=tiles, margins=False)
+    assert psnr(img[:, mask], o64["img"][:, mask]) >= 50.0
+    assert (np.abs(img - o64["img"]).max(axis=0)[mask] <= 2e-3).mean() >= 0.999
+    print(f"\n[full size] {n} splats, {mism} borderline list differences on {len(tiles)} tiles, "
+          f"TC PSNR {psnr(imgtc[:, mask], o['img'][:, mask]):.1f} dB (FP32 inputs), "
+          f"{psnr(img[:, mask], o64['img'][:, mask]):.1f} dB (whole frame)")
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
