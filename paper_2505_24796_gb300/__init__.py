@@ -449,9 +449,49 @@ class FramePipeline:
     host link).  Every frame's copies are issued by ``submit``; ``synchronize`` waits for all.
 
       pipe = FramePipeline(renderer, precision="tc_fp16_split")
-      pipe.submit(host_scene, host_img)   # host tensors (pinned); returns at once
+      host_scene = FramePipeline.pinned_scene(scene)   # the arrays in one pinned buffer
+      pipe.submit(host_scene, host_img)                # returns at once
       pipe.synchronize()
+
+    A scene from ``pinned_scene`` goes up in one copy (its arrays are views of one pinned buffer, laid
+    out as the device slot); any other dict of pinned tensors goes up array by array.
     """
+
+    _ALIGN = 256
+
+    @staticmethod
+    def _layout(arrays: dict):
+        """Byte offsets of the arrays in one buffer (each 256-byte aligned) and the total size."""
+        offs, off = {}, 0
+        for k, v in arrays.items():
+            offs[k] = off
+            off += (v.numel() * v.element_size() + FramePipeline._ALIGN - 1) // FramePipeline._ALIGN * FramePipeline._ALIGN
+        return offs, off
+
+    @staticmethod
+    def _views(buf: torch.Tensor, like: dict, offs: dict) -> dict:
+        out = {}
+        for k, v in like.items():
+            n = v.numel() * v.element_size()
+            out[k] = buf[offs[k]:offs[k] + n].view(v.dtype).view(v.shape)
+        return out
+
+    @staticmethod
+    def pinned_scene(scene: dict) -> dict:
+        """The scene's arrays (numpy or torch) copied into views of one pinned host buffer, which
+        ``submit`` uploads in one copy; non-array entries (sh_degree) are kept."""
+        arrays = {k: (torch.from_numpy(np.ascontiguousarray(v)) if isinstance(v, np.ndarray) else v.contiguous().cpu())
+                  for k, v in scene.items() if isinstance(v, (np.ndarray, torch.Tensor))}
+        offs, total = FramePipeline._layout(arrays)
+        buf = torch.empty(total, dtype=torch.uint8).pin_memory()
+        out = FramePipeline._views(buf, arrays, offs)
+        for k, v in arrays.items():
+            out[k].copy_(v)
+        out["_buffer"] = buf
+        for k, v in scene.items():
+            if not isinstance(v, (np.ndarray, torch.Tensor)):
+                out[k] = v
+        return out
 
     def __init__(self, renderer: "Renderer", precision="tc_fp16_split", **render_kw):
         self.r = renderer
@@ -469,21 +509,28 @@ class FramePipeline:
         self.n = 0
 
     def _slot_scene(self, slot, host_scene):
+        arrays = {k: v for k, v in host_scene.items() if isinstance(v, torch.Tensor) and k != "_buffer"}
         if self.scenes[slot] is None:
-            self.scenes[slot] = {k: torch.empty(v.shape, dtype=v.dtype, device=self.device)
-                                 for k, v in host_scene.items() if isinstance(v, torch.Tensor)}
+            offs, total = self._layout(arrays)
+            buf = torch.empty(total, dtype=torch.uint8, device=self.device)
+            self.scenes[slot] = self._views(buf, arrays, offs)
+            self.scenes[slot]["_buffer"] = buf
             self.scenes[slot]["sh_degree"] = int(host_scene["sh_degree"])
         return self.scenes[slot]
 
     def submit(self, host_scene: dict, host_img: torch.Tensor):
         slot = self.n & 1
         dsc = self._slot_scene(slot, host_scene)
+        hbuf = host_scene.get("_buffer")
         with torch.cuda.stream(self.copy_stream):
             if self.scene_free[slot] is not None:
                 self.copy_stream.wait_event(self.scene_free[slot])
-            for k, v in host_scene.items():
-                if isinstance(v, torch.Tensor):
-                    dsc[k].copy_(v, non_blocking=True)
+            if hbuf is not None and hbuf.numel() == dsc["_buffer"].numel():
+                dsc["_buffer"].copy_(hbuf, non_blocking=True)   # one copy: same layout on both sides
+            else:
+                for k, v in host_scene.items():
+                    if isinstance(v, torch.Tensor) and k != "_buffer":
+                        dsc[k].copy_(v, non_blocking=True)
             copied = self.copy_stream.record_event()
         cs = self.compute_stream
         cs.wait_event(copied)

@@ -342,10 +342,13 @@ def test_frame_pipeline_matches_direct_frames(tc):
     P = len(sc["opacity"])
     cap = 4 * int(oracle.project(cam, scene64(sc))["tiles_touched"].sum()) + 64
     variants = []
-    for f in (1.0, 0.4, 0.8, 0.25, 1.0):
-        v = {k: (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() if isinstance(x, np.ndarray) else x)
-             for k, x in sc.items()}
-        v["opacity"] = (v["opacity"] * f).pin_memory()
+    for i, f in enumerate((1.0, 0.4, 0.8, 0.25, 1.0)):
+        s2 = dict(sc, opacity=(np.asarray(sc["opacity"]) * f).astype(np.float32))
+        if i % 2:   # arrays in one pinned buffer: one copy a frame
+            v = tc.FramePipeline.pinned_scene(s2)
+        else:       # separate pinned arrays: a copy per array
+            v = {k: (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() if isinstance(x, np.ndarray) else x)
+                 for k, x in s2.items()}
         variants.append(v)
     r = tc.Renderer(cam, P, cap, device=DEV)
     pipe = tc.FramePipeline(r)
@@ -355,7 +358,7 @@ def test_frame_pipeline_matches_direct_frames(tc):
     pipe.synchronize()
     r2 = tc.Renderer(cam, P, cap, device=DEV)
     for v, h in zip(variants, host):
-        d = {k: (x.to(DEV) if isinstance(x, torch.Tensor) else x) for k, x in v.items()}
+        d = {k: (x.to(DEV) if isinstance(x, torch.Tensor) else x) for k, x in v.items() if k != "_buffer"}
         out = r2.frame(d)
         torch.cuda.synchronize()
         assert torch.equal(out["img"].cpu(), h)
