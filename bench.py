@@ -731,6 +731,24 @@ def run_tcgs(args):
     rl_render["tensor_frac"] = rl_render["tensor_tflops"] / rl_render["tensor_peak_tflops"]
     # what bounds it: instruction issue (warp instructions from the capture over the live time, against
     # 4 issue slots per SM per clock)
+    # the special-function unit: one ex2 per walked (pixel, Gaussian) slot, against its throughput
+    # measured here (tcgs_microbench_ex2: 8 blocks of 256 threads per SM, 8 independent chains each)
+    ex2_out = torch.empty(SM_COUNT * 8 * 256, dtype=torch.float32, device=dev)
+    tc.tcgs_microbench_ex2(ex2_out, SM_COUNT * 8, 256)
+    torch.cuda.synchronize()
+    ex2_rate = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n_ex2 = tc.tcgs_microbench_ex2(ex2_out, SM_COUNT * 8, 2048)
+        e1.record()
+        e1.synchronize()
+        ex2_rate = max(ex2_rate, n_ex2 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    walked_slots = st_tc[2]
+    rl_render["sfu"] = {"achieved": walked_slots / (render_ms * 1e-3) / 1e9, "peak": ex2_rate, "unit": "G ex2/s",
+                        "frac": walked_slots / (render_ms * 1e-3) / 1e9 / ex2_rate,
+                        "source": "one ex2 per walked slot (the TC path's executed fragment slots); peak measured "
+                                  "in this run by tcgs_microbench_ex2"}
     n_inst = ncu_traffic("k_render_tc", args.scale, key="warp_instructions")
     if n_inst is not None:
         issue_peak = SM_COUNT * 4 * SM_MAX_MHZ * 1e6 / 1e9

@@ -394,6 +394,14 @@ TCGS_API tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam /* host */, int32
  */
 TCGS_API tcgs_status tcgs_selftest_bounded_wait(int32_t* device_status, uint32_t polls, tcgs_stream stream);
 
+/*
+ * Microbenchmark of the special-function unit: `blocks` blocks of 256 threads, each thread running 8
+ * independent chains of `iters` base-2 exponentials (ex2.approx.ftz.f32, the one transcendental
+ * the tensor-core renderer evaluates per walked slot), so blocks x 256 x 8 x iters exponentials in
+ * all; out: device float [blocks x 256] (a checksum).  Timed by the caller (CUDA events).
+ */
+TCGS_API tcgs_status tcgs_microbench_ex2(float* out, int32_t blocks, int32_t iters, tcgs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_GLOBAL, TCG
 TILE = 16
 
 __all__ = ["tcgs_project", "tcgs_project_bwd", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
-           "tcgs_bin_sort_exact", "tcgs_tile_order", "tcgs_selftest_bounded_wait",
+           "tcgs_bin_sort_exact", "tcgs_tile_order", "tcgs_selftest_bounded_wait", "tcgs_microbench_ex2",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
            "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS", "FramePipeline",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
@@ -176,6 +176,16 @@ def tcgs_selftest_bounded_wait(device_status, polls: int = 4096, stream=None) ->
     polls and writes TCGS_ERR_TIMEOUT to device_status (device int32)."""
     check("tcgs_selftest_bounded_wait", _L().tcgs_selftest_bounded_wait(
         _ptr(device_status, torch.int32, "device_status"), int(polls), _stream(stream)))
+
+
+def tcgs_microbench_ex2(out: torch.Tensor, blocks: int, iters: int, stream=None) -> int:
+    """Enqueues blocks x 256 x 8 x iters ex2.approx evaluations (out: device float [blocks x 256]);
+    returns that count for the caller's timing."""
+    if out.numel() < blocks * 256:
+        raise ValueError("out needs blocks x 256 floats")
+    check("tcgs_microbench_ex2", _L().tcgs_microbench_ex2(_ptr(out, torch.float32, "out"), int(blocks), int(iters),
+                                                          _stream(stream)))
+    return blocks * 256 * 8 * iters
 
 
 def tcgs_tile_order(cam, tile_ranges, out=None, stream=None) -> torch.Tensor:

@@ -73,6 +73,8 @@ def test_invalid_arguments_rejected_on_host(lib):
         _lib.TCGS_ERR_INVALID   # conic and opacity required
     assert lib.tcgs_selftest_bounded_wait(V, 16, None) == _lib.TCGS_ERR_INVALID          # no status word
     assert lib.tcgs_selftest_bounded_wait(ctypes.c_void_p(256), 0, None) == _lib.TCGS_ERR_INVALID   # no polls
+    assert lib.tcgs_microbench_ex2(V, 1, 1, None) == _lib.TCGS_ERR_INVALID
+    assert lib.tcgs_microbench_ex2(ctypes.c_void_p(256), 0, 1, None) == _lib.TCGS_ERR_INVALID
 
 
 def test_build_targets_sm103a_only():
