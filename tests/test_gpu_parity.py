@@ -520,6 +520,20 @@ def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
           f"{psnr(img[:, mask], o64['img'][:, mask]):.1f} dB (whole frame)")
 
 
+def test_ex2_microbenchmark_runs_its_chains(tc):
+    """tcgs_microbench_ex2: every thread's 8 chains x <- -2^x settle at the fixed point of
+    x = -2^x (about -0.6412), so each checksum is about 8 times it."""
+    out = torch.full((2 * 256,), float("nan"), device=DEV)
+    n = tc.tcgs_microbench_ex2(out, 2, 64)
+    torch.cuda.synchronize()
+    assert n == 2 * 256 * 8 * 64
+    v = out.cpu().numpy()
+    x = -0.5
+    for _ in range(200):
+        x = -2.0 ** x
+    np.testing.assert_allclose(v, 8 * x, rtol=1e-4)
+
+
 # ------------------------------------------------------------------ alpha blending
 
 def margin_mask(o, cull_tol, term_tol):
