@@ -38,8 +38,8 @@ SM_COUNT, SM_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # `ncu --set full` capture summarised in the named profile.  They are reported only while the
 # kernel's sources hash to the value they had when the counters were taken.
 NCU_TRAFFIC = {
-    "k_render_tc": {"bytes": 43562752 + 9327872, "warp_instructions": 191046439,
-                    "sha256": "a47dcf3dc87407ba1be8ee889142c669be338cd805664e4e7d2f3b5e3dfadcea",
+    "k_render_tc": {"bytes": 43582208 + 9316608, "warp_instructions": 191046439,
+                    "sha256": "3ad0e9ec063422d9119d16044742b16838cd5348c3282d3482504f604d749b4b",
                     "sources": ["paper_2505_24796_gb300/csrc/render_tc.cu", "paper_2505_24796_gb300/csrc/common.cuh"],
                     "profile": "profiles/k_render_tc_precision_1920x1080.md"},
 }
@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 1M Gaussians (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the differentiation, scheduler and large workloads (reported beside the headline)")
+                    help="skip the plain, differentiation, scheduler and large workloads (reported beside the headline)")
     ap.add_argument("--sched-train-views", type=int, default=200)
     ap.add_argument("--large-frames", type=int, default=0, metavar="P",
                     help="profiling run: two frames of the large workload's distribution with P Gaussians, "
@@ -225,6 +225,40 @@ def _events_ms(fn, reps, warmup, flush=None):
     return statistics.median(ts)
 
 
+def bench_plain(dev, flush, stream, steps=50, warmup=5):
+    """128x128, 1,000 Gaussians, SH0: whole frames of both renderers, each replayed as one CUDA graph
+    with the L2 flushed before every frame (at this size a frame is bound by launch latency)."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    from paper_2505_24796_gb300 import scenes
+    cam, sc = scenes.plain_forward()
+    d = tc.scene_to_device(sc, dev)
+    pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    r = tc.Renderer(cam, len(sc["opacity"]), n + 1024, device=dev, stats=True)
+    r.frame(d, precision="fp32")
+    torch.cuda.synchronize()
+    st = r.stats.to(torch.int64).sum(0).tolist()
+    img32 = r.out["img"].clone()
+    r.stats = None
+    out = {"workload": "plain: 128x128, fx=fy=128, 1,000 Gaussians, SH0; exact tile coverage",
+           "splats": int(r.bins["n_splats"].item()), "alpha_evals": st[0] + st[1]}
+    for prec in ("tc_fp16_split", "fp32"):
+        tot, stg = time_frames(r, d, prec, steps, warmup, True, flush, stream)
+        ms = statistics.median(tot)
+        out[prec] = {"frames_per_s": 1000.0 / ms, "frame_ms": ms,
+                     "stages_ms": dict(zip(["project", "bin_sort", "render_fwd"],
+                                           [statistics.median(x) for x in stg]))}
+    out["speedup_frame"] = out["fp32"]["frame_ms"] / out["tc_fp16_split"]["frame_ms"]
+    out["speedup_render"] = (out["fp32"]["stages_ms"]["render_fwd"] /
+                             out["tc_fp16_split"]["stages_ms"]["render_fwd"])
+    r.frame(d, precision="tc_fp16_split")
+    torch.cuda.synchronize()
+    diff = (r.out["img"] - img32).abs().max().item()
+    out["max_abs_tc_vs_fp32"] = diff
+    return out
+
+
 def bench_differentiation(dev, flush):
     """1280x720, 500k Gaussians: forward and backward of the alpha-blending stage (L1 loss to a seeded
     target); the loss gradient itself is user code and is formed outside the timed events."""
@@ -270,6 +304,8 @@ def bench_differentiation(dev, flush):
             "alpha_evals": st[0] + st[1], "f_blend": st[0],
             "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
                    "render_fwd_tc": fwdtc, "render_bwd": bwd_ms, "project_bwd": pbwd_ms},
+            "frames_per_s_fwd": {"tc_fp16_split": 1000.0 / (proj_ms + bin_ms + fwdtc),
+                                 "fp32": 1000.0 / (proj_ms + bin_ms + fwd32)},
             "train_step_ms_fp32": proj_ms + bin_ms + fwd32 + bwd_ms + pbwd_ms,
             "train_step_ms_tc_fwd": proj_ms + bin_ms + fwdtc + bwd_ms + pbwd_ms,
             "train_step_note": "forward and backward to the 3D parameters (means, scales, quaternions, opacity, "
@@ -772,7 +808,8 @@ def run_tcgs(args):
     if not args.no_extras:
         del r
         torch.cuda.empty_cache()
-        for name, fn in (("differentiation", lambda: bench_differentiation(dev, flush)),
+        for name, fn in (("plain", lambda: bench_plain(dev, flush, stream)),
+                         ("differentiation", lambda: bench_differentiation(dev, flush)),
                          ("scheduler", lambda: bench_scheduler(dev, args.sched_train_views)),
                          ("large", lambda: bench_large(dev, flush))):
             try:

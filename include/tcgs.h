@@ -103,7 +103,9 @@ typedef struct {
     const uint32_t* tile_order; /* nullable device [num_tiles]: TC precisions in tile-local coordinates
                                 render with a persistent grid (4 CTAs per SM) that takes the tiles in this
                                 order, a permutation of all tiles such as tcgs_tile_order's (the order
-                                changes the schedule, never the image); NULL: one CTA per tile */
+                                changes the schedule, never the image); NULL: one CTA per tile.  A view
+                                of at most tcgs_tc_wave_tiles() tiles is rendered one CTA per tile even
+                                when an order is given: every tile then starts in the first wave */
     uint32_t* work_counter;  /* device uint32, required with tile_order: the grid's next-tile counter,
                                 zeroed by the call */
 } tcgs_render_opts;
@@ -271,6 +273,14 @@ TCGS_API tcgs_status tcgs_render_fwd(const tcgs_camera* cam /* host */, const tc
  */
 TCGS_API tcgs_status tcgs_tile_order(const tcgs_camera* cam /* host */, const uint32_t* tile_ranges,
                                      uint32_t* tile_order, tcgs_stream stream);
+
+/*
+ * Tiles the tensor-core renderer keeps resident at once on the current device (4 CTAs per SM; 608 on
+ * a 152-SM GB300), or 0 when the device is not sm_103.  A view with at most this many tiles starts
+ * every tile in the first wave, where no order can shorten the schedule: tcgs_render_fwd then ignores
+ * tile_order (and leaves work_counter alone), so a caller may skip tcgs_tile_order for such views.
+ */
+TCGS_API int32_t tcgs_tc_wave_tiles(void);
 
 /* Largest number of views one batched launch can render. */
 #define TCGS_MAX_VIEWS 16

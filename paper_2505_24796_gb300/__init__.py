@@ -25,7 +25,7 @@ from ._lib import (PRECISIONS, TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_GLOBAL, TCG
 TILE = 16
 
 __all__ = ["tcgs_project", "tcgs_project_bwd", "tcgs_bin_sort", "tcgs_bin_sort_workspace_size", "tcgs_bin_sort_noalloc",
-           "tcgs_bin_sort_exact", "tcgs_tile_order", "tcgs_selftest_bounded_wait", "tcgs_microbench_ex2",
+           "tcgs_bin_sort_exact", "tcgs_tile_order", "tcgs_tc_wave_tiles", "tcgs_selftest_bounded_wait", "tcgs_microbench_ex2",
            "tcgs_render_fwd", "tcgs_render_bwd", "tcgs_render_fwd_batched", "tcgs_tile_features", "tcgs_feature_norm",
            "tcgs_mlp_fwd", "tcgs_mlp_bwd", "tcgs_adam_step", "tcgs_sched_order", "tcgs_frag2mat_beta", "make_camera", "render_opts", "Renderer", "rasterize", "render_gaussians", "TcgsError", "PRECISIONS", "FramePipeline",
            "TCGS_FP32", "TCGS_TC_FP16", "TCGS_TC_FP16_SPLIT", "TCGS_TC_FP8", "TCGS_TC_TF32", "TCGS_TC_FP16_GLOBAL",
@@ -186,6 +186,12 @@ def tcgs_microbench_ex2(out: torch.Tensor, blocks: int, iters: int, stream=None)
     check("tcgs_microbench_ex2", _L().tcgs_microbench_ex2(_ptr(out, torch.float32, "out"), int(blocks), int(iters),
                                                           _stream(stream)))
     return blocks * 256 * 8 * iters
+
+
+def tcgs_tc_wave_tiles() -> int:
+    """Tiles the tensor-core renderer keeps resident at once on the current device (0 when it is not
+    sm_103): views with no more tiles than this render one CTA per tile, without a tile order."""
+    return int(_L().tcgs_tc_wave_tiles())
 
 
 def tcgs_tile_order(cam, tile_ranges, out=None, stream=None) -> torch.Tensor:
@@ -388,8 +394,9 @@ class Renderer:
         exact_tiles (default): keep only the tiles each Gaussian reaches with alpha >= 1/255
         (tcgs_bin_sort_exact: the same images as the rectangle's tiles, shorter lists); False bins
         every tile of the rectangle (tcgs_bin_sort).  persistent (default): the tensor-core renders
-        take the tiles longest list first on a persistent grid (tcgs_tile_order); the image is the
-        same as with one CTA per tile."""
+        take the tiles longest list first on a persistent grid (tcgs_tile_order) when the view has
+        more tiles than one wave of CTAs holds (tcgs_tc_wave_tiles); the image is the same as with
+        one CTA per tile."""
         self.cam = _cam(cam)
         self.tight_radius = bool(tight_radius)
         self.exact_tiles = bool(exact_tiles)
@@ -414,6 +421,7 @@ class Renderer:
                       if stats else None)
         self.device_status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.persistent = bool(persistent)
+        self._wave_tiles = None
         self.tile_order = torch.empty(self.num_tiles, dtype=torch.int32, device=dev)
         self.work_counter = torch.zeros(1, dtype=torch.int32, device=dev)
 
@@ -436,7 +444,9 @@ class Renderer:
     def render(self, opacity, precision="tc_fp16_split", alpha_max=0.99, early_cull=None, bg=(0, 0, 0),
                stream=None, tile_cull=True):
         order = None
-        if self.persistent and precision in _PERSISTENT_PRECISIONS:
+        if self.persistent and precision in _PERSISTENT_PRECISIONS and self._wave_tiles is None:
+            self._wave_tiles = tcgs_tc_wave_tiles()
+        if self.persistent and precision in _PERSISTENT_PRECISIONS and self.num_tiles > self._wave_tiles:
             order = tcgs_tile_order(self.cam, self.bins["tile_ranges"], out=self.tile_order, stream=stream)
         opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status, tile_cull,
                            tile_order=order, work_counter=self.work_counter if order is not None else None)

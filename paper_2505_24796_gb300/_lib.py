@@ -74,6 +74,7 @@ SIGNATURES = {
     "tcgs_frag2mat_beta": (c_int32, [P_CAM, c_int32, V, V, V, V, V, c_int32, V, c_int32, V, V, V]),
     "tcgs_selftest_bounded_wait": (c_int32, [V, ctypes.c_uint32, V]),
     "tcgs_microbench_ex2": (c_int32, [V, c_int32, c_int32, V]),
+    "tcgs_tc_wave_tiles": (c_int32, []),
 }
 
 _lock = threading.Lock()

@@ -775,10 +775,11 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
     p.tile_cull = p.global ? 0 : opts->tile_cull;   // the ablation walks every entry
     p.early_cull = opts->early_cull;
     const int tiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
-    if (opts->tile_order && !p.global) {
+    if (opts->tile_order && !opts->work_counter) return TCGS_ERR_INVALID;
+    if (opts->tile_order && !p.global && tiles > g_sm_count * kTcCtasPerSm) {
         // persistent grid over the tiles in the given order: each CTA allocates TMEM and builds U
-        // once, and the longest lists start first
-        if (!opts->work_counter) return TCGS_ERR_INVALID;
+        // once, and the longest lists start first (with at most one wave of tiles every tile starts
+        // at once, so the plain grid below runs without the counter's reset)
         p.queue = opts->tile_order;
         p.queue_tiles = 1;
         p.n_items = (uint32_t)tiles;
@@ -890,6 +891,11 @@ extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precis
     p.status = device_status;
     p.dbg_tiles = tiles; p.dbg_max_n = max_n; p.dbg_beta = beta_out;
     return launch_tc<true, false, false>(p, n_tiles, (cudaStream_t)stream);
+}
+
+extern "C" int32_t tcgs_tc_wave_tiles(void) {
+    using namespace tcgs;
+    return device_is_sm103() ? g_sm_count * kTcCtasPerSm : 0;
 }
 
 extern "C" tcgs_status tcgs_selftest_bounded_wait(int32_t* device_status, uint32_t polls, tcgs_stream stream) {

@@ -365,31 +365,54 @@ def test_frame_pipeline_matches_direct_frames(tc):
     assert not torch.equal(host[0], host[1])
 
 
-@pytest.mark.parametrize("name,make", SMALL[1:])
+PERSISTENT_SCENES = SMALL[1:] + [
+    ("precision_crop_640x400", lambda: scenes.precision(P=40_000, width=640, height=400, seed=15)),
+    ("large_crop_960x540", lambda: scenes.large(P=20_000, width=960, height=540, seed=14)),
+]
+
+
+@pytest.mark.parametrize("name,make", PERSISTENT_SCENES)
 def test_persistent_render_matches_one_cta_per_tile(tc, name, make):
-    """The persistent TC renderer (tiles taken longest list first, tcgs_tile_order) gives the image,
-    T and n_contrib of one CTA per tile bit for bit, for every tile-local encoding; its order is a
-    permutation of the tiles with non-increasing list-length groups."""
+    """With a tile order (tcgs_tile_order), the TC renderer gives the image, T and n_contrib of one
+    CTA per tile bit for bit, for every tile-local encoding.  Views of more tiles than one wave of CTAs
+    (tcgs_tc_wave_tiles) run the persistent grid, which pops the work counter; smaller views run one
+    CTA per tile and leave the counter alone.  The order is a permutation of the tiles with
+    non-increasing list-length groups."""
     cam, sc = make()
     dsc = {k: to_torch(v, DEV) if isinstance(v, np.ndarray) else v for k, v in sc.items()}
     P = len(sc["opacity"])
     cap = int(oracle.project(cam, scene64(sc))["tiles_touched"].sum()) + 64
-    outs = {}
-    for persistent in (False, True):
-        r = tc.Renderer(cam, P, cap, device=DEV, persistent=persistent)
-        r.project(dsc)
-        r.bin_sort()
-        for prec in ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8"):
-            o = r.render(dsc["opacity"], prec)
-            torch.cuda.synchronize()
-            outs[(persistent, prec)] = {k: v.clone() for k, v in o.items()}
-        if persistent:
-            order = r.tile_order.cpu().numpy()
-            lens = np.diff(r.bins["tile_ranges"].cpu().numpy(), axis=1).ravel().astype(np.int64)
+    wave = tc.tcgs_tc_wave_tiles()
+    assert wave == 4 * torch.cuda.get_device_properties(0).multi_processor_count
+    r = tc.Renderer(cam, P, cap, device=DEV, persistent=False)
+    r.project(dsc)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    n_tiles = r.num_tiles
+    order = tc.tcgs_tile_order(r.cam, r.bins["tile_ranges"])
+    sentinel = 0x5A5A5A5A
+    counter = torch.full((1,), sentinel, dtype=torch.int32, device=DEV)
     for prec in ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8"):
-        a, b = outs[(False, prec)], outs[(True, prec)]
+        a = {k: v.clone() for k, v in r.render(dsc["opacity"], prec).items()}
+        counter.fill_(sentinel)
+        opts = tc.render_opts(prec, tile_order=order, work_counter=counter)
+        b = tc.tcgs_render_fwd(r.cam, opts, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"],
+                               r.proj["conic"], dsc["opacity"], r.proj["rgb"])
+        torch.cuda.synchronize()
         for k in ("img", "T_final", "n_contrib"):
             assert torch.equal(a[k], b[k]), (prec, k)
+        popped = int(counter.item()) != sentinel
+        assert popped == (n_tiles > wave), (prec, n_tiles, wave)
+        if n_tiles > wave:   # every tile popped once, plus one failed pop per CTA
+            assert int(counter.item()) == n_tiles + wave
+    rp = tc.Renderer(cam, P, cap, device=DEV)   # the default Renderer picks the same path itself
+    rp.project(dsc)
+    rp.bin_sort()
+    o = rp.render(dsc["opacity"], "tc_fp16_split")
+    torch.cuda.synchronize()
+    assert torch.equal(o["img"], r.render(dsc["opacity"], "tc_fp16_split")["img"])
+    order = order.cpu().numpy()
+    lens = np.diff(r.bins["tile_ranges"].cpu().numpy(), axis=1).ravel().astype(np.int64)
     np.testing.assert_array_equal(np.sort(order), np.arange(len(lens)))
     groups = np.where(lens[order] > 0, np.floor(np.log2(np.maximum(lens[order], 1))) + 1, 0)
     assert (np.diff(groups) <= 0).all()
