@@ -174,7 +174,9 @@ TCGS_API size_t tcgs_bin_sort_workspace_size(int32_t P, int64_t splat_capacity, 
  * pixel square [16 tx, 16 tx + 16) x [16 ty, 16 ty + 16), r = radius[g] > 0.
  * The order is the (tile, depth-bits) key order of the paper's radix sort; it is produced by
  * an LSD radix sort whose depth digits run before duplication (on P keys) and whose tile
- * digits run after it (on N keys).
+ * digits run after it (on N keys).  A small view (at most 256 tiles, P <= 8192 and
+ * splat_capacity <= 32768) runs the same passes in two single-CTA kernels (4 launches in all,
+ * against about 20), with the same result.
  * In:  mean2d [P,2], radius [P], depth [P] (> 0 where radius > 0).
  * Out: ids_sorted [splat_capacity] uint32 (first N entries valid), tile_ranges [num_tiles, 2]
  *      uint32 [start, end), n_splats: device int64 = N, status: device int32 (TCGS_OK, or

@@ -846,6 +846,130 @@ __global__ void __launch_bounds__(kThreads) k_ranges(const uint32_t* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- small views in one CTA
+
+// Views of at most kSmallMaxTiles tiles with at most kSmallMaxP Gaussians and a splat capacity of at
+// most kSmallMaxCapacity sort in two single-CTA kernels instead of the multi-block passes, whose
+// launches (about 20, each a few microseconds) would otherwise be most of such a frame.  The passes
+// are the same stable LSD passes, so the lists are the same.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int32_t kSmallMaxP = 8192;
+constexpr int64_t kSmallMaxCapacity = 32768;
+constexpr int kSmallMaxTiles = kRadix;   // the tile id is then a single 8-bit digit
+
+struct SmallSortSmem {
+    uint32_t wcnt[kSmallWarps][kRadix];   // per round: count, then start, of each (warp, digit)
+    uint32_t hist[kRadix];                // digit counts of the pass
+    uint32_t next[kRadix];                // next output position of each digit
+    uint32_t ws[kSmallWarps];
+};
+
+// One stable LSD pass of the whole CTA over n items, digit (key >> shift) & mask (mask <= 255):
+// digit counts, their exclusive scan, then rounds of 1024 consecutive items, each ranked inside its
+// warp by __match_any_sync and placed after the same digit's items of the lower warps and of the
+// earlier rounds.  keys_in and keys_out are distinct buffers; the CTA's last barrier makes the output
+// visible to all its threads.
+// No __restrict__: the depth kernel reads in one pass what its own threads wrote in the previous one,
+// so these loads must not take the read-only path.
+__device__ void cta_radix_pass(SmallSortSmem& sm, const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                               uint32_t* vout, uint32_t n, int shift, uint32_t mask) {
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t < kRadix) sm.hist[t] = 0u;
+    __syncthreads();
+    for (uint32_t i = t; i < n; i += kSmallThreads) atomicAdd(&sm.hist[(kin[i] >> shift) & mask], 1u);
+    __syncthreads();
+    uint32_t total;
+    const uint32_t start = block_exclusive_scan<uint32_t, kSmallThreads>(t < kRadix ? sm.hist[t] : 0u, sm.ws, total);
+    if (t < kRadix) sm.next[t] = start;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t* flat = &sm.wcnt[0][0];
+    for (uint32_t r0 = 0; r0 < n; r0 += kSmallThreads) {
+        for (int j = t; j < kSmallWarps * kRadix; j += kSmallThreads) flat[j] = 0u;
+        __syncthreads();
+        const uint32_t i = r0 + (uint32_t)t;
+        const bool valid = i < n;
+        uint32_t k = 0u, v = 0u, d = 0x100u | (uint32_t)lane;   // past the end: a value no digit takes
+        if (valid) {
+            k = kin[i];
+            v = vin[i];
+            d = (k >> shift) & mask;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && rank == 0u) sm.wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (t < kRadix) {   // thread t owns digit t: starts over the warps in warp order
+            uint32_t run = sm.next[t];
+            for (int w = 0; w < kSmallWarps; ++w) {
+                const uint32_t c = sm.wcnt[w][t];
+                sm.wcnt[w][t] = run;
+                run += c;
+            }
+            sm.next[t] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = sm.wcnt[warp][d] + rank;   // < n: the digit counts sum to n
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+}
+
+// Depth order of the P Gaussians (4 passes, a-buffers -> b -> a -> b -> a), the splat offsets in that
+// order, N and the capacity check: the multi-block depth passes and the three scan kernels in one CTA.
+__global__ void __launch_bounds__(kSmallThreads) k_small_depth_scan(uint32_t P, uint32_t* dk_a, uint32_t* dv_a,
+                                                                    uint32_t* dk_b, uint32_t* dv_b,
+                                                                    const uint32_t* __restrict__ counts,
+                                                                    uint32_t* __restrict__ offsets, int64_t capacity,
+                                                                    int64_t* __restrict__ n_splats,
+                                                                    int32_t* __restrict__ status,
+                                                                    uint32_t* __restrict__ n_u32) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ SmallSortSmem sm;
+    __shared__ unsigned long long ws64[kSmallWarps];
+    for (int pass = 0; pass < 4; ++pass) {
+        const bool even = (pass & 1) == 0;
+        cta_radix_pass(sm, even ? dk_a : dk_b, even ? dv_a : dv_b, even ? dk_b : dk_a, even ? dv_b : dv_a, P,
+                       8 * pass, 0xFFu);
+    }
+    unsigned long long run = 0;
+    for (uint32_t r0 = 0; r0 < P; r0 += kSmallThreads) {
+        const uint32_t i = r0 + threadIdx.x;
+        unsigned long long tot;
+        const unsigned long long ex =
+            block_exclusive_scan<unsigned long long, kSmallThreads>(i < P ? counts[dv_a[i]] : 0ull, ws64, tot);
+        if (i < P) offsets[i] = (uint32_t)(run + ex);   // read only when N fits the capacity (< 2^32)
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        *n_splats = (int64_t)run;
+        const bool ok = run <= (unsigned long long)capacity;
+        *status = ok ? TCGS_OK : TCGS_ERR_CAPACITY;
+        *n_u32 = ok ? (uint32_t)run : 0u;
+    }
+}
+
+// Stable sort of the N splats by tile id (one 8-bit digit) and the tile ranges from its digit counts
+// (tiles without splats keep the [0, 0) the key kernel wrote).
+__global__ void __launch_bounds__(kSmallThreads) k_small_tile_sort(const uint32_t* kin, const uint32_t* vin,
+                                                                   uint32_t* kout, uint32_t* vout,
+                                                                   const uint32_t* __restrict__ n_u32, int num_tiles,
+                                                                   uint32_t* __restrict__ ranges) {
+    pdl_wait();
+    __shared__ SmallSortSmem sm;
+    cta_radix_pass(sm, kin, vin, kout, vout, *n_u32, 0, 0xFFu);
+    const int t = threadIdx.x;
+    if (t < num_tiles && sm.hist[t]) {
+        ranges[2 * t] = sm.next[t] - sm.hist[t];
+        ranges[2 * t + 1] = sm.next[t];
+    }
+}
+
 // ---------------------------------------------------------------- workspace
 
 struct Workspace {
@@ -968,6 +1092,32 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
                    w.dv_a, w.counts, tile_ranges, 2 * num_tiles, w.digit_total);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
+    const bool small = P <= kSmallMaxP && splat_capacity <= kSmallMaxCapacity && num_tiles <= kSmallMaxTiles;
+    if (small) {
+        // 1-2 in one CTA
+        launch_pdl(k_small_depth_scan, 1, kSmallThreads, 0, s, (uint32_t)P, w.dk_a, w.dv_a, w.dk_b, w.dv_b, w.counts,
+                   w.offsets, splat_capacity, n_splats, status, w.n_u32);
+        count_launches(1);
+        TCGS_CHECK_LAUNCH();
+        if (splat_capacity == 0 || P == 0) return TCGS_OK;
+        // 3. duplication, 4-5. one CTA: the tile sort into ids_sorted and the ranges
+        const int dup_blocks = (P + kThreads - 1) / kThreads;
+        if (rows)
+            launch_pdl(k_duplicate<true, true>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, w.dv_a, w.offsets,
+                       w.counts, mean2d, radius, conic, opacity, w.sk_b, w.sv_b, w.n_u32);
+        else if (exact)
+            launch_pdl(k_duplicate<true, false>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, w.dv_a, w.offsets,
+                       w.counts, mean2d, radius, conic, opacity, w.sk_b, w.sv_b, w.n_u32);
+        else
+            launch_pdl(k_duplicate<false, false>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, w.dv_a, w.offsets,
+                       w.counts, mean2d, radius, conic, opacity, w.sk_b, w.sv_b, w.n_u32);
+        count_launches(1);
+        launch_pdl(k_small_tile_sort, 1, kSmallThreads, 0, s, w.sk_b, w.sv_b, w.sk_a, ids_sorted, w.n_u32, num_tiles,
+                   tile_ranges);
+        count_launches(1);
+        TCGS_CHECK_LAUNCH();
+        return TCGS_OK;
+    }
     // 1. depth order (4 passes; the result returns to the a-buffers)
     int pass = 0;
     if (P > 0) {

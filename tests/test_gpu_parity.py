@@ -123,6 +123,46 @@ def test_bin_sort_bit_exact(tc, name, make):
     np.testing.assert_array_equal(out["tile_ranges"].cpu().numpy(), b["ranges"])
 
 
+SMALL_VIEW_SCENES = [
+    ("plain_128", lambda: scenes.plain_forward()),
+    ("plain_ragged_200x136", lambda: scenes.plain_forward(P=1500, width=200, height=136, seed=11)),
+    ("plain_8192_128x128", lambda: scenes.plain_forward(P=8192, width=128, height=128, seed=16)),
+]
+
+
+@pytest.mark.parametrize("exact", [False, True])
+@pytest.mark.parametrize("name,make", SMALL_VIEW_SCENES)
+def test_bin_sort_small_view_path_matches_multi_block_path(tc, name, make, exact):
+    """A view of at most 256 tiles with P <= 8192 sorts in two single-CTA kernels when the capacity
+    is at most 32768, and in the multi-block passes above it: the same N, lists and ranges either
+    way (with the row path too, at 32 P), and the oracle's lists for the rectangle coverage."""
+    cam, sc = make()
+    pr = oracle.project(cam, scene64(sc))
+    inp = dict(mean2d=f32(pr["mean2d"]), radius=pr["radius"], depth=f32(pr["depth"]), conic=f32(pr["conic"]))
+    P = len(sc["opacity"])
+    b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"])
+    m = to_torch(inp["mean2d"], DEV); r = to_torch(inp["radius"].astype(np.int32), DEV)
+    d = to_torch(inp["depth"], DEV)
+    kw = dict(conic=to_torch(inp["conic"], DEV), opacity=to_torch(sc["opacity"], DEV)) if exact else {}
+    caps = [b["n"] + 17] + ([32 * P + 5] if 32 * P + 5 <= 32768 else []) + [40_000]
+    assert caps[0] <= 32768 and caps[-1] > 32768
+    res = []
+    for cap in caps:
+        out = tc.tcgs_bin_sort(cam, m, r, d, capacity=cap, **kw)
+        torch.cuda.synchronize()
+        assert int(out["status"].item()) == 0
+        n = int(out["n_splats"].item())
+        res.append((n, out["ids_sorted"].cpu().numpy()[:n], out["tile_ranges"].cpu().numpy()))
+    for n, ids, ranges in res[1:]:
+        assert n == res[0][0]
+        np.testing.assert_array_equal(ids, res[0][1])
+        np.testing.assert_array_equal(ranges, res[0][2])
+    if not exact:
+        assert res[0][0] == b["n"]
+        np.testing.assert_array_equal(res[0][1], b["ids"])
+        np.testing.assert_array_equal(res[0][2], b["ranges"])
+
+
 def test_bin_sort_capacity_overflow_reports_status(tc):
     cam, sc = scenes.plain_forward()
     pr = oracle.project(cam, scene64(sc))
