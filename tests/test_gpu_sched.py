@@ -137,7 +137,7 @@ def test_learned_order_beats_list_length(tc):
     mse_mlp, mse_len = np.mean((pred - yt) ** 2), np.mean((base - yt) ** 2)
     print(f"\n[scheduler] train loss {final:.4f}; held-out MSE of log cost: MLP {mse_mlp:.4f}, list length {mse_len:.4f}")
     assert mse_mlp < mse_len
-    # schedule quality judged on the measured per-tile work
+    # schedule quality assessed on the measured per-tile work
     walked = np.expm1(yt)
     workers = 152 * 3
     qm = test.queue("mlp", model).cpu().numpy()
