@@ -77,5 +77,13 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.tcgs_microbench_ex2(ctypes.c_void_p(256), 0, 1, None) == _lib.TCGS_ERR_INVALID
 
 
+def test_wave_query_reports_no_tc_device_without_a_gpu(lib):
+    """tcgs_tc_wave_tiles answers 0 when the current device is not an sm_103 GPU (here: none)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present; the GPU tests check the wave size")
+    assert lib.tcgs_tc_wave_tiles() == 0
+
+
 def test_build_targets_sm103a_only():
     assert tbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
