@@ -160,6 +160,67 @@ def test_projection_numeric_jacobian():
         assert lam1 >= lam.max() * (1 - 1e-6)
 
 
+def _pinhole_cam_jacobian(cam, pc):
+    """Central-difference Jacobian (2 x 3) of the pinhole map (X, Y, Z) -> (fx X / Z + cx, fy Y / Z + cy)
+    at the camera-space point pc."""
+    def proj(p):
+        return np.array([cam["fx"] * p[0] / p[2] + cam["cx"], cam["fy"] * p[1] / p[2] + cam["cy"]])
+    h = 1e-6 * max(1.0, float(np.abs(pc).max()))
+    return np.stack([(proj(pc + h * e) - proj(pc - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+
+
+@pytest.mark.parametrize("view", ["identity", "rotated"])
+def test_projection_frustum_clamp_of_the_jacobian(view):
+    """Gaussians beyond the frustum: x/z and y/z are clamped to +-1.3 tan(fov / 2) where J is built
+    (3DGS convention), so Sigma' must equal J_num Sigma_cam J_num^T + 0.3 I with J_num the numerical
+    Jacobian of the pinhole map taken at the point of the same depth on the clamped ray, while mean2d
+    keeps the unclamped projection.  Cases: x beyond the right edge, y beyond the top, both beyond
+    on the negative side, and one inside (no clamp); width != height and fx != fy, so a limit taken
+    from the wrong axis, a missing 1.3, a clamp of X instead of X / Z or a clamped mean all fail."""
+    rng = np.random.default_rng(5)
+    vm = np.hstack([np.eye(3), np.zeros((3, 1))]) if view == "identity" else _random_view(rng)
+    cam = scenes.pinhole(640, 360, fx=500.0, fy=420.0, viewmat=vm)
+    cam["viewmat"] = vm
+    R3, t3 = vm[:, :3], vm[:, 3]
+    limx, limy = 1.3 * 320 / 500.0, 1.3 * 180 / 420.0
+    z = 4.0
+    cases = [(1.25 * limx, 0.1), (0.2, -1.3 * limy), (-1.2 * limx, -1.4 * limy), (0.5 * limx, 0.5 * limy)]
+    for (rx, ry) in cases:
+        pc = np.array([rx * z, ry * z, z])
+        mu = np.linalg.solve(R3, pc - t3)
+        scales = np.array([0.9, 0.5, 0.7])   # wide enough to reach the image from outside the frustum
+        q = rng.standard_normal(4)
+        sc = make_scene(mu, scales, q, [0.9], [[0.5, 0.5, 0.5]])
+        pr = oracle.project(cam, sc)
+        assert pr["radius"][0] > 0, (rx, ry)
+        pcl = np.array([np.clip(rx, -limx, limx) * z, np.clip(ry, -limy, limy) * z, z])
+        J = _pinhole_cam_jacobian(cam, pcl)
+        Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        S_cam = R3 @ (Rg @ np.diag(scales ** 2) @ Rg.T) @ R3.T
+        ref = J @ S_cam @ J.T + 0.3 * np.eye(2)
+        a, b, c = pr["cov2d"][0]
+        np.testing.assert_allclose([a, b, c], [ref[0, 0], ref[0, 1], ref[1, 1]], rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(pr["mean2d"][0], [500.0 * rx + 320.0, 420.0 * ry + 180.0], rtol=1e-12)
+
+
+def test_projection_frustum_clamp_isotropic_closed_form():
+    """Isotropic Gaussian (Sigma = s^2 I, identity view) at camera point (X, Y, Z) with X / Z past the
+    limit: with xc = 1.3 tan(fov_x / 2) Z (the clamped abscissa) and Y inside,
+    Sigma' = s^2 J J^T + 0.3 I, J = [[fx / Z, 0, -fx xc / Z^2], [0, fy / Z, -fy Y / Z^2]], so
+    a = s^2 fx^2 (1 + (xc / Z)^2) / Z^2 + 0.3, b = s^2 fx fy xc Y / Z^4, c = s^2 fy^2 (1 + (Y / Z)^2) / Z^2 + 0.3."""
+    fx, fy, W, H = 600.0, 500.0, 800, 400
+    cam = scenes.pinhole(W, H, fx=fx, fy=fy)
+    s, Z, X, Y = 1.0, 5.0, 5.0, 0.7
+    sc = make_scene([X, Y, Z], [s, s, s], [0.4, 0.1, -0.7, 0.2], [0.9], [[0.5, 0.5, 0.5]])
+    pr = oracle.project(cam, sc)
+    xc = 1.3 * (W / 2 / fx) * Z
+    assert X > xc and pr["radius"][0] > 0
+    a = s * s * fx * fx * (1 + (xc / Z) ** 2) / Z ** 2 + 0.3
+    b = s * s * fx * fy * xc * Y / Z ** 4
+    c = s * s * fy * fy * (1 + (Y / Z) ** 2) / Z ** 2 + 0.3
+    np.testing.assert_allclose(pr["cov2d"][0], [a, b, c], rtol=1e-12)
+
+
 def test_projection_culls_behind_near_plane():
     cam = scenes.pinhole(64, 64, fx=64.0)
     sc = make_scene([[0, 0, 0.1], [0, 0, -3], [0, 0, 2]], np.full((3, 3), 0.05), np.tile([1, 0, 0, 0], (3, 1)),
