@@ -34,14 +34,13 @@ WORKLOAD = ("precision: 1 view 1920x1080, fx=fy=1100, 1M Gaussians from a 64-clu
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 SM_COUNT, SM_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) and executed warp
-# instructions (smsp__inst_executed.sum) of the render kernel on this workload, from the
-# `ncu --set full` capture summarised in the named profile.  They are reported only while the
-# kernel's sources hash to the value they had when the counters were taken.
+# instructions (smsp__inst_executed.sum) of the render kernel on this workload, from one
+# `ncu --set full` capture of this command's kernel.  They are reported only while the kernel's
+# sources hash to the value they had when the counters were taken.
 NCU_TRAFFIC = {
     "k_render_tc": {"bytes": 43582208 + 9316608, "warp_instructions": 191046439,
                     "sha256": "3ad0e9ec063422d9119d16044742b16838cd5348c3282d3482504f604d749b4b",
-                    "sources": ["paper_2505_24796_gb300/csrc/render_tc.cu", "paper_2505_24796_gb300/csrc/common.cuh"],
-                    "profile": "profiles/k_render_tc_precision_1920x1080.md"},
+                    "sources": ["paper_2505_24796_gb300/csrc/render_tc.cu", "paper_2505_24796_gb300/csrc/common.cuh"]},
 }
 
 
@@ -156,29 +155,26 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_frame_estimate(cam, sc, tile_fraction, seed=0):
-    """Time the FP64 oracle on one bounded sample of a frame: projection and binning of the whole
-    scene, Algorithm 1 on a random subset of tiles; returns (seconds per full frame, sample info)."""
+def _scene64(sc):
+    return {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+
+
+def oracle_frame_single(cam, s64):
+    """One whole frame of the FP64 oracle on one host thread: projection and binning of the whole
+    scene, Algorithm 1 on every tile.  Returns (seconds, info with the image)."""
     import oracle
-    s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
     t0 = time.perf_counter()
     pr = oracle.project(cam, s64)
     t1 = time.perf_counter()
     b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
     t2 = time.perf_counter()
-    gw, gh = oracle.grid(cam)
-    nt = gw * gh
-    k = max(1, int(round(nt * tile_fraction)))
-    tiles = np.random.default_rng(seed).choice(nt, k, replace=False)
-    o = oracle.render(cam, b, pr["mean2d"], pr["conic"], s64["opacity"], pr["rgb"], tiles=tiles, margins=False)
+    o = oracle.render(cam, b, pr["mean2d"], pr["conic"], s64["opacity"], pr["rgb"], margins=False)
     t3 = time.perf_counter()
-    est = (t1 - t0) + (t2 - t1) + (t3 - t2) * nt / k
-    info = dict(project_s=t1 - t0, bin_s=t2 - t1, render_sample_s=t3 - t2, tiles_sampled=k, tiles=nt,
-                cpu_work_s=t3 - t0, frame_s_est=est, img=o["img"], tiles_list=tiles)
-    return est, info
+    gw, gh = oracle.grid(cam)
+    return t3 - t0, dict(project_s=t1 - t0, bin_s=t2 - t1, render_s=t3 - t2, tiles=gw * gh, img=o["img"])
 
 
-def oracle_frame_all_cores(cam, sc, threads=None):
+def oracle_frame_all_cores(cam, s64, threads=None):
     """The FP64 oracle on one whole frame with every host core: projection and binning as they stand
     (single-threaded), then Algorithm 1 on the tiles dealt round-robin to one thread per core (the C
     renderer keeps no global state, and ctypes releases the GIL for the call); the threads' images
@@ -187,7 +183,6 @@ def oracle_frame_all_cores(cam, sc, threads=None):
     import concurrent.futures as cf
     import oracle
     threads = threads or len(os.sched_getaffinity(0))
-    s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
     t0 = time.perf_counter()
     pr = oracle.project(cam, s64)
     b = oracle.bin_sort(cam, pr["mean2d"], pr["radius"], pr["depth"])
@@ -204,27 +199,32 @@ def oracle_frame_all_cores(cam, sc, threads=None):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, as it stands, single-threaded on the host."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores.  Every step, warm-up
+    included, is one whole frame of the bench workload (projection and binning single-threaded,
+    Algorithm 1 on all tiles dealt to one thread per core); the line reports the mean of the timed
+    frames, measured, not extrapolated.  Under torchrun only rank 0 runs it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cam, sc = workload(args.scale)
-    frac = 1.0 / 64
-    times = []
+    s64 = _scene64(sc)
+    times, n_thr = [], 1
     for i in range(args.warmup + args.steps):
-        est, info = oracle_frame_estimate(cam, sc, frac, seed=i)
+        t, n_thr, _ = oracle_frame_all_cores(cam, s64)
         if i >= args.warmup:
-            times.append(est)
+            times.append(t)
     t = statistics.mean(times)
     v = 1.0 / t
+    gw, gh = (cam["width"] + 15) // 16, (cam["height"] + 15) // 16
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "P": len(sc["opacity"])},
-        "cpu_baseline": {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: FP64 projection + binning of the whole scene, Algorithm 1 on "
-                                   f"{frac:.4f} of the tiles (random, seeded per step), extrapolated to the frame"},
+        "config": {"workload": WORKLOAD, "P": len(sc["opacity"]), "coverage": "square (3-sigma)"},
+        "cpu_baseline": {"value": v, "unit": "frames/s", "cores": n_thr, "kind": "oracle",
+                         "sample": f"every step one whole frame: FP64 projection + binning of the whole scene "
+                                   f"(one thread) and Algorithm 1 on all {gw * gh} tiles dealt to {n_thr} threads; "
+                                   f"mean of {args.steps} timed frames after {args.warmup} warm-up frames"},
         "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -732,19 +732,15 @@ def run_tcgs(args):
     cpu_baseline = cpu_all = None
     acc = {"psnr_tc_vs_fp32_db": (10 * math.log10(1 / mse_tc_fp32) if mse_tc_fp32 > 0 else None)}
     if not args.no_cpu_baseline and world == 1:   # the host-core baseline is taken at N = 1 only
-        est, info = oracle_frame_estimate(cam, sc, 1.0, seed=1)   # the whole frame
-        est2, info2 = oracle_frame_estimate(cam, sc, 1.0, seed=2)
-        est = 0.5 * (est + est2)
-        info["cpu_work_s"] += info2["cpu_work_s"]
+        s64 = _scene64(sc)
+        t1, info = oracle_frame_single(cam, s64)
+        t2, _ = oracle_frame_single(cam, s64)
+        est = 0.5 * (t1 + t2)
         cpu_baseline = {"value": 1.0 / est, "unit": "frames/s", "cores": 1, "kind": "oracle",
                         "sample": f"two whole frames: FP64 projection + binning of the whole scene and "
                                   f"Algorithm 1 on all {info['tiles']} tiles, mean of the two; "
-                                  f"{info['cpu_work_s']:.1f} s of CPU work"}
-        gw = (W + 15) // 16
-        mask = np.zeros((H, W), bool)
-        for t in info["tiles_list"]:
-            ty, tx = divmod(int(t), gw)
-            mask[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
+                                  f"{t1 + t2:.1f} s of CPU work"}
+        mask = np.ones((H, W), bool)
         oimg = info["img"]
         for name, im in (("tc", img_tc_np), ("fp32", img32_np)):
             d = (im - oimg)[:, mask]
@@ -754,7 +750,7 @@ def run_tcgs(args):
             acc[f"max_abs_{name}"] = float(np.abs(d).max())
         acc["oracle_pixels_compared"] = int(mask.sum())
         try:   # the same oracle on every host core, reported beside the single-thread baseline
-            t_all, n_thr, img_all = oracle_frame_all_cores(cam, sc)
+            t_all, n_thr, img_all = oracle_frame_all_cores(cam, s64)
             cpu_all = {"value": 1.0 / t_all, "unit": "frames/s", "cores": n_thr, "kind": "oracle",
                        "sample": f"one whole frame: FP64 projection + binning (single-threaded, as the oracle "
                                  f"stands) and Algorithm 1 on all {info['tiles']} tiles dealt to {n_thr} threads",
@@ -790,7 +786,7 @@ def run_tcgs(args):
     stage_names = ["project", "bin_sort", "render_fwd"]
     stage_ms = [statistics.mean(s) for s in stg]
     # the dominant kernel: k_render_tc is the longest single launch of the frame (bin_sort is a stage
-    # of 17 launches, the longest of them a tenth of the render; profiles/launches_*.md)
+    # of 17 launches, the longest of them a tenth of the render in the ncu launch list)
     dominant = "render_fwd"
     ops = alpha_evals * 1 + f_blend * 8   # EarlyCull compare per evaluated fragment + 8 FP32 ops per blend
     alu_peak = SM_COUNT * SM_LANES * SM_MAX_MHZ * 1e6 / 1e12   # thread-ops/s at max clock, TOP/s
