@@ -231,7 +231,10 @@ TCGS_API tcgs_status tcgs_bin_sort_exact(const tcgs_camera* cam /* host */, int3
  *     return TCGS_ERR_SCRATCH_LIMIT at once (nothing enqueued).  64 MiB holds, for example,
  *     P = 1,000 Gaussians with 5.4 million splats, or P = 500,000 with 4.5 million.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
- *     that device current) and caches it; make that first call before any stream capture.
+ *     that device current) and caches it with the device's current CUDA context; make that first
+ *     call before any stream capture.  A call that finds another context current on the device
+ *     (after cudaDeviceReset, or after the primary context was released and created again) looks
+ *     the address up again, so it too should come before any capture.
  *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
  *   - All calls share the one array and it keeps whatever the previous call left there; the
  *     kernels initialise every scratch word they read, so no clearing is needed between calls.

@@ -15,6 +15,8 @@
 // digit turns the counts into global output offsets.  scatter: each warp ranks its 32-key
 // rounds with __match_any_sync, warps and tiles are chained in order, so the pass is stable.
 // No block ever waits on another block.
+#include <cuda.h>
+
 #include <mutex>
 #include <type_traits>
 
@@ -1003,21 +1005,24 @@ inline Workspace layout(char* base, int64_t P, int64_t cap) {
 
 // Blocks of the scatter kernel resident at once on the current device (one full wave: each block
 // then walks a contiguous run of tiles, and no second, partly filled wave is left at the end).
+// Looked up once per device and instance, under a lock (callers may sort on several devices from
+// several host threads).
 template <int KI>
 inline int resident_sort_blocks() {
-    static int cached_dev = -1, cached = 0;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 256;
-    if (dev != cached_dev) {
-        int sms = 0, per_sm = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static std::mutex mu;
+    static int cached[kMaxDevices] = {};
+    DeviceInfo d;
+    if (!current_device_info(&d)) return 256;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[d.device] == 0) {
+        int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter<KI>, kThreads, 0);
-        cached = sms * (per_sm > 0 ? per_sm : 1);
-        if (cached < 1) cached = 256;
-        if (cached > kMaxBlocks) cached = kMaxBlocks;
-        cached_dev = dev;
+        int c = d.sms * (per_sm > 0 ? per_sm : 1);
+        if (c < 1) c = 256;
+        if (c > kMaxBlocks) c = kMaxBlocks;
+        cached[d.device] = c;
     }
-    return cached;
+    return cached[d.device];
 }
 
 template <int KI>
@@ -1380,14 +1385,37 @@ extern "C" tcgs_status tcgs_sched_order(const float* cost, const uint32_t* items
 // ---------------------------------------------------------------- allocation-free variant
 //
 // The scratch array every tcgs_bin_sort_noalloc call works in.  Host code must not pass its name
-// to a kernel (on the host it is only a stand-in symbol): the device address is looked up once
-// per device with cudaGetSymbolAddress and passed on as an ordinary workspace pointer.
+// to a kernel (on the host it is only a stand-in symbol): the device address is looked up with
+// cudaGetSymbolAddress, with the device current, and passed on as an ordinary workspace pointer.
+// The address belongs to the CUDA context the module was loaded in, so it is cached per device
+// together with that context and looked up again when the device's current context is another one
+// (after cudaDeviceReset, or a release and re-creation of the primary context).
 static __device__ __align__(256) unsigned char g_bin_sort_scratch[TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxNoallocDevices = 64;
 std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxNoallocDevices] = {};
+void* g_scratch_addr[tcgs::kMaxDevices] = {};
+CUcontext g_scratch_ctx[tcgs::kMaxDevices] = {};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+bool g_ctx_fn_looked_up = false;
+
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent, reached through the
+// runtime's entry-point query, so the library needs no link against the driver library), or null.
+// Called with g_scratch_mutex held.
+CUcontext current_context() {
+    if (!g_ctx_fn_looked_up) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+        g_ctx_fn_looked_up = true;
+    }
+    CUcontext c = nullptr;
+    if (!g_ctx_get_current || g_ctx_get_current(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 }  // namespace
 
 extern "C" tcgs_status tcgs_bin_sort_noalloc(const tcgs_camera* cam, int32_t P, const float* mean2d,
@@ -1400,14 +1428,16 @@ extern "C" tcgs_status tcgs_bin_sort_noalloc(const tcgs_camera* cam, int32_t P, 
     const size_t need = tcgs_bin_sort_workspace_size(P, splat_capacity, dc.grid_w * dc.grid_h);
     if (need > (size_t)TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES) return TCGS_ERR_SCRATCH_LIMIT;
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxNoallocDevices) return TCGS_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= tcgs::kMaxDevices) return TCGS_ERR_CUDA;
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_addr[dev]) {
-            void* p = nullptr;
+        CUcontext ctx = current_context();
+        if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
+            void* p = nullptr;   // set-up on this device and context (the lookup also makes the context current)
             if (cudaGetSymbolAddress(&p, g_bin_sort_scratch) != cudaSuccess || !p) return TCGS_ERR_CUDA;
             g_scratch_addr[dev] = p;
+            g_scratch_ctx[dev] = current_context();
         }
         scratch = g_scratch_addr[dev];
     }

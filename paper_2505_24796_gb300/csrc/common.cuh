@@ -153,6 +153,16 @@ __device__ __forceinline__ void set_status(int32_t* st, int code) {
 namespace tcgs {
 // host-side count of kernel launches (tcgs_kernel_launches)
 void count_launches(unsigned n);
+
+// Properties of the current device, looked up once per device (thread-safe).  Returns false when no
+// device is current or its index is beyond kMaxDevices.
+constexpr int kMaxDevices = 64;
+struct DeviceInfo {
+    int device;   // index of the current device
+    int sms;      // streaming multiprocessors
+    bool sm103;   // compute capability 10.3 (the tensor-core paths need sm_103a)
+};
+bool current_device_info(DeviceInfo* out);
 }
 
 #define TCGS_CHECK_LAUNCH()                                  \
