@@ -146,6 +146,15 @@ def differentiation(P=500_000, width=1280, height=720, seed=3):
     return cam, scene, target
 
 
+def wide_field(P=3000, width=160, height=96, seed=17):
+    """Parity case for the frustum clamp: a 160x96 view (fx = fy = 128) of Gaussians whose means
+    spread to about three times the half field of view (x, y in [-6, 6], z in [2, 10]), with
+    log-scales N(-1.5, 0.5) so that many of those outside the frustum still reach the image."""
+    rng = np.random.default_rng(seed)
+    cam = pinhole(width, height, fx=128.0)
+    return cam, uniform_box(rng, P, xy=6.0, log_scale=(-1.5, 0.5))
+
+
 RESOLUTIONS = [(640, 480), (800, 600), (1024, 768), (1280, 720), (1600, 900), (1920, 1080)]
 SCENE_CENTRE = np.array([0.0, 0.0, 6.0])
 

@@ -43,3 +43,27 @@ def to_torch(a, dev, dtype=None):
     if dtype is not None:
         t = t.to(dtype)
     return t.to(dev)
+
+
+def margin_mask(o, cull_tol=1e-5, term_tol=1e-4):
+    """Pixels whose cull or termination decision lies near its threshold in the oracle's arithmetic,
+    where FP32 may decide it the other way: |beta + ln 255| < cull_tol (the FP32 exponent carries an
+    error of about 1e-6 here) or |ln(T - alpha T) - ln 1e-4| < term_tol (T is a product over up to
+    thousands of blends, each adding about 6e-8 of relative error)."""
+    return (o["cull_margin"] < cull_tol) | (o["term_margin"] < term_tol)
+
+
+def gaussians_at_pixels(b, cam, pixels, n_eval, n_contrib_gpu):
+    """Boolean mask over Gaussians: those a pixel of `pixels` (boolean [H, W]) evaluates on either
+    side, i.e. its tile's list up to one past the later of the oracle's evaluation count and the
+    GPU's last blended index.  A flipped decision at such a pixel changes the transmittance of every
+    later fragment there and the colour blended behind every earlier one."""
+    gw = (int(cam["width"]) + 15) // 16
+    P = int(b["ids"].max()) + 1 if b["n"] > 0 else 0
+    out = np.zeros(P, bool)
+    for py, px in zip(*np.nonzero(pixels)):
+        t = (py // 16) * gw + px // 16
+        s, e = b["ranges"][t]
+        k = min(e - s, max(int(n_eval[py, px]), int(n_contrib_gpu[py, px]) + 1) + 1)
+        out[b["ids"][s:s + k]] = True
+    return out

@@ -13,7 +13,7 @@ import oracle
 from oracle import frag2mat as f2m
 from paper_2505_24796_gb300 import scenes
 
-from .helpers import f32, oracle_frame, psnr, scene64, to_torch
+from .helpers import f32, gaussians_at_pixels, oracle_frame, psnr, scene64, to_torch
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,9 +46,18 @@ SMALL = [
 
 # ------------------------------------------------------------------ projection
 
-@pytest.mark.parametrize("name,make", SMALL)
+# projection cases: the small workloads plus a view whose Gaussians reach the image from up to three
+# half-fields outside it, so the frustum clamp of the Jacobian is active for many of them
+PROJ = SMALL + [("wide_field_160x96", lambda: scenes.wide_field())]
+
+
+@pytest.mark.parametrize("name,make", PROJ)
 @pytest.mark.parametrize("tight", [False, True])
 def test_project_matches_oracle(tc, name, make, tight):
+    """Projection against the FP64 oracle.  The conic is the inverse of Sigma', whose FP32 entries
+    carry a few ulps of relative error; inverting a 2 x 2 matrix multiplies that by its condition
+    number kappa, so each Gaussian's conic must be within 128 ulps x kappa of the oracle's, relative
+    to its largest entry (measured: below 16 ulps x kappa)."""
     cam, sc = make()
     pr = oracle.project(cam, scene64(sc), tight_radius=tight)
     dsc = {k: to_torch(v, DEV) for k, v in sc.items() if isinstance(v, np.ndarray)}
@@ -64,11 +73,20 @@ def test_project_matches_oracle(tc, name, make, tight):
     both = vis_o & vis_g
     np.testing.assert_allclose(g["mean2d"][both], pr["mean2d"][both], rtol=2e-6, atol=2e-4)
     np.testing.assert_allclose(g["depth"][both], pr["depth"][both], rtol=1e-6)
-    scale = np.abs(pr["conic"][both]).max(axis=1, keepdims=True)
-    cerr = np.abs(g["conic"][both] - pr["conic"][both]) / scale
-    print(f"\n[project] {name}: max rel conic err {cerr.max():.3g}, mean2d err "
-          f"{np.abs(g['mean2d'][both] - pr['mean2d'][both]).max():.3g}")
-    assert cerr.max() <= 1e-3
+    scale = np.abs(pr["conic"][both]).max(axis=1)
+    cerr = np.abs(g["conic"][both] - pr["conic"][both]).max(axis=1) / scale
+    a, b, c = pr["cov2d"][both].T
+    half_gap = np.sqrt(0.25 * (a - c) ** 2 + b * b)
+    kappa = (0.5 * (a + c) + half_gap) / (0.5 * (a + c) - half_gap)
+    ulps = cerr / (2.0 ** -24 * kappa)
+    if name.startswith("wide_field"):
+        m = sc["means3"].astype(np.float64)
+        lim = 1.3 * np.array([cam["width"] / (2 * cam["fx"]), cam["height"] / (2 * cam["fy"])])
+        clamped = ((np.abs(m[:, :2] / m[:, 2:]) > lim).any(axis=1))[both]
+        assert clamped.sum() >= 100, clamped.sum()   # the clamp is exercised
+    print(f"\n[project] {name}: max rel conic err {cerr.max():.3g} ({ulps.max():.1f} ulps x kappa, kappa <= "
+          f"{kappa.max():.1f}), mean2d err {np.abs(g['mean2d'][both] - pr['mean2d'][both]).max():.3g}")
+    assert ulps.max() <= 128, ulps.max()
     np.testing.assert_allclose(g["rgb"][both], pr["rgb"][both], atol=2e-6)
     rad_diff = g["radius"][both] != pr["radius"][both]
     assert rad_diff.mean() < 1e-3
@@ -432,7 +450,7 @@ def test_persistent_render_matches_one_cta_per_tile(tc, name, make):
     order = tc.tcgs_tile_order(r.cam, r.bins["tile_ranges"])
     sentinel = 0x5A5A5A5A
     counter = torch.full((1,), sentinel, dtype=torch.int32, device=DEV)
-    for prec in ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8"):
+    for prec in ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8", "fp32_frag2mat"):
         a = {k: v.clone() for k, v in r.render(dsc["opacity"], prec).items()}
         counter.fill_(sentinel)
         opts = tc.render_opts(prec, tile_order=order, work_counter=counter)
@@ -551,7 +569,7 @@ def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
     counter = torch.zeros(1, dtype=torch.int32, device=DEV)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     imgs = {}
-    for prec in ("fp32", "tc_fp16_split"):
+    for prec in ("fp32", "tc_fp16_split", "tc_fp16"):
         opts = tc.render_opts(prec, device_status=status,
                               tile_order=order if prec != "fp32" else None,
                               work_counter=counter if prec != "fp32" else None)
@@ -568,6 +586,13 @@ def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
     imgtc = imgs["tc_fp16_split"][0]
     assert psnr(imgtc[:, mask], o["img"][:, mask]) >= 50.0
     assert (np.abs(imgtc - o["img"]).max(axis=0)[mask] <= 2e-3).mean() >= 0.999
+    # the paper's K = 8 layout (v0 / 3 in three FP16 slots, Sec. 5.1) is recorded, not held to the TC bar:
+    # about 55 dB, but only about 86% of pixels within 2e-3 on this frame, so it fails the 99.9% criterion
+    # (its exponent error reaches ~0.1 where |v0| is large; the split layout is the shipped default)
+    img16 = imgs["tc_fp16"][0]
+    p16 = psnr(img16[:, mask], o["img"][:, mask])
+    w16 = float((np.abs(img16 - o["img"]).max(axis=0)[mask] <= 2e-3).mean())
+    assert 50.0 <= p16 <= 60.0 and 0.75 <= w16 <= 0.95, (p16, w16)
 
     # (2) the whole frame from the scene, as the bench renders it
     d = tc.scene_to_device(sc, DEV)
@@ -579,7 +604,8 @@ def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
     assert psnr(img[:, mask], o64["img"][:, mask]) >= 50.0
     assert (np.abs(img - o64["img"]).max(axis=0)[mask] <= 2e-3).mean() >= 0.999
     print(f"\n[full size] {n} splats, {mism} borderline list differences on {len(tiles)} tiles, "
-          f"TC PSNR {psnr(imgtc[:, mask], o['img'][:, mask]):.1f} dB (FP32 inputs), "
+          f"TC PSNR {psnr(imgtc[:, mask], o['img'][:, mask]):.1f} dB (FP32 inputs), paper K = 8 layout {p16:.1f} dB "
+          f"with {100 * w16:.1f}% within 2e-3, "
           f"{psnr(img[:, mask], o64['img'][:, mask]):.1f} dB (whole frame)")
 
 
@@ -666,10 +692,57 @@ def test_render_tc_split_matches_oracle(tc, name, make, alpha_max):
 
 
 @pytest.mark.parametrize("name,make", SMALL)
+@pytest.mark.parametrize("alpha_max", [0.99, 1.0])
+def test_render_fp32_frag2mat_matches_oracle(tc, name, make, alpha_max):
+    """TCGS_FP32_FRAG2MAT, the tensor-core renderer with its product u^T v on CUDA cores in FP32 (the
+    ablation arm that differs from the TC path only in the product).  Its exponent carries FP32
+    rounding of the tile-local coefficients, a few ulps of sum |u_i v_i|, below the split encoding's
+    error, so it meets the TC criteria (PSNR >= 50 dB, >= 99.9% of pixels within 2e-3) and, away
+    from margin pixels, max |RGB| <= 1e-4 (recorded: about 1e-6); block marks change nothing."""
+    cam, sc = make()
+    _, inp, b, o = oracle_frame(cam, sc, alpha_max=alpha_max)
+    g = gpu_inputs(inp, b)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    imgs = []
+    for cull in (True, False):
+        out = tc.tcgs_render_fwd(cam, tc.render_opts("fp32_frag2mat", alpha_max, device_status=status, tile_cull=cull),
+                                 g["ranges"], g["ids"], g["mean2d"], g["conic"], g["opacity"], g["rgb"])
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        imgs.append({k: v.cpu().numpy() for k, v in out.items()})
+    for k in ("img", "T_final", "n_contrib"):
+        np.testing.assert_array_equal(imgs[0][k], imgs[1][k])
+    img = imgs[0]["img"]
+    err = np.abs(img - o["img"]).max(axis=0)
+    keep = ~margin_mask(o, 1e-4, 1e-4)
+    print(f"\n[fp32_frag2mat] {name} alpha_max={alpha_max}: PSNR {psnr(img, o['img']):.1f} dB, max abs outside "
+          f"margins {err[keep].max():.2e}")
+    assert psnr(img, o["img"]) >= 50.0
+    assert (err <= 2e-3).mean() >= 0.999
+    assert err[keep].max() <= 1e-4
+
+
+# Measured accuracy of the encodings that do not meet the TC criteria (PSNR >= 50 dB and >= 99.9% of
+# pixels within 2e-3 of the FP64 oracle): (PSNR dB, fraction of pixels within 2e-3) per workload.  The
+# paper's K = 8 layout (v0 / 3 in three FP16 slots, Sec. 5.1) and TF32 carry about 11 bits of v, so the
+# exponents of Gaussians far from the tile centre (|v0| up to ~300) are off by up to ~0.1 and the
+# precision crop (small splats, long lists) falls below even 50 dB; the FP8 split keeps ~16 bits.
+RECORDED_ENCODINGS = {
+    ("tc_fp16", "plain_128"): (62.2, 0.949), ("tc_fp16", "plain_ragged_200x136"): (66.1, 0.983),
+    ("tc_fp16", "precision_crop_240x120"): (45.4, 0.568),
+    ("tc_tf32", "plain_128"): (62.4, 0.956), ("tc_tf32", "plain_ragged_200x136"): (66.8, 0.983),
+    ("tc_tf32", "precision_crop_240x120"): (45.4, 0.567),
+    ("tc_fp8", "plain_128"): (77.3, 0.9996), ("tc_fp8", "plain_ragged_200x136"): (77.3, 0.9998),
+    ("tc_fp8", "precision_crop_240x120"): (67.2, 0.981),
+}
+
+
+@pytest.mark.parametrize("name,make", SMALL)
 @pytest.mark.parametrize("precision", ["tc_fp16", "tc_tf32", "tc_fp8"])
-def test_render_tc_other_encodings_report_error(tc, name, make, precision):
-    """The paper's K = 8 layout (v0 / 3 three times), TF32 and the FP8 split: accuracy is
-    reported, with a loose floor."""
+def test_render_tc_other_encodings_recorded_error(tc, name, make, precision):
+    """The paper's K = 8 layout, TF32 and the FP8 split, against the FP64 oracle: their measured
+    accuracy (RECORDED_ENCODINGS) is reproduced to within 1 dB and 1% of pixels, and each falls short
+    of the TC criteria on the precision crop (the split FP16 layout, the default, meets them)."""
     cam, sc = make()
     _, inp, b, o = oracle_frame(cam, sc)
     g = gpu_inputs(inp, b)
@@ -680,9 +753,12 @@ def test_render_tc_other_encodings_report_error(tc, name, make, precision):
     assert int(status.item()) == 0
     img = out["img"].cpu().numpy()
     p = psnr(img, o["img"])
-    print(f"\n[{precision}] {name}: PSNR {p:.2f} dB, within 2e-3: "
-          f"{(np.abs(img - o['img']).max(axis=0) <= 2e-3).mean():.5f}")
-    assert p >= 30.0
+    within = float((np.abs(img - o["img"]).max(axis=0) <= 2e-3).mean())
+    print(f"\n[{precision}] {name}: PSNR {p:.2f} dB, within 2e-3: {within:.5f}")
+    rp, rw = RECORDED_ENCODINGS[(precision, name)]
+    assert abs(p - rp) <= 1.0 and abs(within - rw) <= 0.01, (p, within)
+    if name.startswith("precision"):
+        assert not (p >= 50.0 and within >= 0.999)
 
 
 def test_render_outputs_empty_tiles_background(tc):
@@ -790,6 +866,10 @@ def test_global_coordinates_collapse_in_fp16(tc):
 
 @pytest.mark.parametrize("name,make", SMALL[:2])
 def test_backward_matches_oracle_gradient(tc, name, make):
+    """Backward kernel against the oracle's analytic gradient (pinned by FP64 finite differences).
+    Every Gaussian that no counted margin pixel evaluates is checked: per Gaussian and gradient
+    array, |gpu - oracle| <= 1e-4 x (its largest oracle component + 1e-3 x the array's largest);
+    the excluded ones are exactly those evaluated at a margin pixel (helpers.gaussians_at_pixels)."""
     cam, sc = make()
     _, inp, b, o = oracle_frame(cam, sc)
     g = gpu_inputs(inp, b)
@@ -802,15 +882,20 @@ def test_backward_matches_oracle_gradient(tc, name, make):
                                g["opacity"], g["rgb"], fwd["img"], fwd["T_final"], fwd["n_contrib"],
                                to_torch(gimg, DEV))
     torch.cuda.synchronize()
-    # Gaussians touching a decision-margin pixel may legitimately differ
-    excl = margin_mask(o, 1e-4, 1e-4)
-    for key, rk in [("dmean2d", "dmean2d"), ("dconic", "dconic"), ("dopacity", "dopacity"), ("drgb", "drgb")]:
-        a = grads[key].cpu().numpy().reshape(len(inp["opacity"]), -1)
-        r = ref[rk].reshape(len(inp["opacity"]), -1)
-        scale = np.abs(r).max(axis=1, keepdims=True) + 1e-3 * np.abs(r).max()
-        rel = np.abs(a - r) / scale
-        bad = (rel > 1e-4).any(axis=1)
-        assert bad.mean() <= max(excl.mean() * 50, 2e-3), (key, bad.sum(), float(rel.max()))
+    P = len(inp["opacity"])
+    margin = margin_mask(o, 1e-4, 1e-4)
+    assert margin.mean() < 1e-3
+    excl = np.zeros(P, bool)
+    ex = gaussians_at_pixels(b, cam, margin, o["n_eval"], fwd["n_contrib"].cpu().numpy())
+    excl[:len(ex)] = ex
+    print(f"\n[backward] {name}: {int(margin.sum())} margin pixels, {int(excl.sum())} of {P} Gaussians excluded")
+    for key in ("dmean2d", "dconic", "dopacity", "drgb"):
+        a = grads[key].cpu().numpy().reshape(P, -1)
+        r = ref[key].reshape(P, -1)
+        scale = np.abs(r).max(axis=1) + 1e-3 * np.abs(r).max()
+        rel = (np.abs(a - r).max(axis=1) / scale)[~excl]
+        print(f"  {key}: rel err 99.9% {np.quantile(rel, 0.999):.2e}, max {rel.max():.2e}")
+        assert rel.max() <= 1e-4, (key, int((rel > 1e-4).sum()), float(rel.max()))
 
 
 def test_autograd_function_matches_backward(tc):

@@ -53,13 +53,19 @@ def test_mlp_forward_backward_match_oracle(tc):
     np.testing.assert_allclose(1 / nm[8:], X.astype(np.float64).std(0), rtol=1e-4)
     y = tc.tcgs_mlp_fwd(to_torch(params, DEV), norm, dX).cpu().numpy()
     yr, _ = osc.mlp_forward(params.astype(np.float64), nm, X, fp16=True)
-    close = np.abs(y - yr) <= 2e-3 * (1 + np.abs(yr))
-    assert close.mean() >= 0.995 and np.abs(y - yr).max() < 0.05
+    err = np.abs(y - yr)
+    close = err <= 2e-3 * (1 + np.abs(yr))
+    print(f"\n[mlp fwd] max abs err {err.max():.3e}, 99.9% {np.quantile(err, 0.999):.3e}, rows beyond "
+          f"2e-3 (1 + |y|): {int((~close).sum())} of {len(y)}")
+    assert close.mean() >= 0.995 and err.max() < 0.05
     loss = torch.zeros(1, device=DEV)
     grad, _ = tc.tcgs_mlp_bwd(to_torch(params, DEV), norm, dX, to_torch(t, DEV), loss=loss)
     torch.cuda.synchronize()
     gr, lr = osc.mlp_backward(params.astype(np.float64), nm, X, t, fp16=True)
     g = grad.cpu().numpy()
+    ge = np.abs(g - gr)
+    print(f"[mlp bwd] max abs err {ge.max():.3e} (max |grad| {np.abs(gr).max():.3e}), max rel err "
+          f"{(ge / (np.abs(gr) + 1e-6 * np.abs(gr).max())).max():.3e}")
     np.testing.assert_allclose(g, gr, rtol=5e-3, atol=2e-3 * np.abs(gr).max())
     assert abs(float(loss.item()) - lr) <= 1e-3 * lr
 
@@ -92,7 +98,7 @@ def test_sched_order_matches_oracle(tc):
     np.testing.assert_array_equal(q, osc.order(key, items))
 
 
-def _small_multiview(tc, n_views, seed, P=200_000, scale=0.25):
+def _small_multiview(tc, n_views, seed, P=200_000, scale=0.25, precision="tc_fp16_split"):
     from paper_2505_24796_gb300.sched import MultiView
     rng = np.random.default_rng(seed)
     scene = scenes.uniform_box(rng, P)
@@ -100,11 +106,14 @@ def _small_multiview(tc, n_views, seed, P=200_000, scale=0.25):
     for c in cams:   # reduced resolutions keep the test fast
         w, h = int(c["width"] * scale), int(c["height"] * scale)
         c.update(width=w, height=h, fx=c["fx"] * scale, fy=c["fy"] * scale, cx=w / 2.0, cy=h / 2.0)
-    return MultiView(scene, cams)
+    return MultiView(scene, cams, precision=precision)
 
 
-def test_batched_render_equals_per_view_render(tc):
-    mv = _small_multiview(tc, 3, 40)
+@pytest.mark.parametrize("precision", ["tc_fp16_split", "fp32_frag2mat"])
+def test_batched_render_equals_per_view_render(tc, precision):
+    """The batched persistent render gives every view's per-view image bit for bit, whatever the
+    queue order, with the tensor-core product and with the same kernel's CUDA-core product."""
+    mv = _small_multiview(tc, 3, 40, precision=precision)
     mv.render_each(stats=False)
     torch.cuda.synchronize()
     ref = [r.out["img"].clone() for r in mv.views]
