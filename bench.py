@@ -268,7 +268,7 @@ def bench_plain(dev, flush, stream, steps=50, warmup=5):
     r.stats = None
     out = {"workload": "plain: 128x128, fx=fy=128, 1,000 Gaussians, SH0; exact tile coverage",
            "splats": int(r.bins["n_splats"].item()), "alpha_evals": st[0] + st[1]}
-    for prec in ("tc_fp16_split", "fp32"):
+    for prec in ("tc_fp16_split", "fp32", "fp32_frag2mat"):
         tot, stg = time_frames(r, d, prec, steps, warmup, True, flush, stream)
         ms = statistics.median(tot)
         out[prec] = {"frames_per_s": 1000.0 / ms, "frame_ms": ms,
@@ -277,6 +277,8 @@ def bench_plain(dev, flush, stream, steps=50, warmup=5):
     out["speedup_frame"] = out["fp32"]["frame_ms"] / out["tc_fp16_split"]["frame_ms"]
     out["speedup_render"] = (out["fp32"]["stages_ms"]["render_fwd"] /
                              out["tc_fp16_split"]["stages_ms"]["render_fwd"])
+    out["speedup_render_vs_fp32_same_skip"] = (out["fp32_frag2mat"]["stages_ms"]["render_fwd"] /
+                                               out["tc_fp16_split"]["stages_ms"]["render_fwd"])
     r.frame(d, precision="tc_fp16_split")
     torch.cuda.synchronize()
     diff = (r.out["img"] - img32).abs().max().item()
@@ -314,6 +316,7 @@ def bench_differentiation(dev, flush):
                            grads=grads)
     fwd32 = _events_ms(lambda: r.render(d["opacity"], "fp32"), 10, 3, flush)
     fwdtc = _events_ms(lambda: r.render(d["opacity"], "tc_fp16_split"), 10, 3, flush)
+    fwdcc = _events_ms(lambda: r.render(d["opacity"], "fp32_frag2mat"), 10, 3, flush)
     r.render(d["opacity"], "fp32")
     bwd_ms = _events_ms(bwd, 10, 3, flush)
     proj_ms = _events_ms(lambda: r.project(d), 10, 3, flush)
@@ -328,7 +331,9 @@ def bench_differentiation(dev, flush):
             "splats": n_exact, "square_coverage": square,
             "alpha_evals": st[0] + st[1], "f_blend": st[0],
             "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
-                   "render_fwd_tc": fwdtc, "render_bwd": bwd_ms, "project_bwd": pbwd_ms},
+                   "render_fwd_tc": fwdtc, "render_fwd_fp32_same_skip": fwdcc, "render_bwd": bwd_ms,
+                   "project_bwd": pbwd_ms},
+            "speedup_render": {"vs_fp32": fwd32 / fwdtc, "vs_fp32_same_skip": fwdcc / fwdtc},
             "frames_per_s_fwd": {"tc_fp16_split": 1000.0 / (proj_ms + bin_ms + fwdtc),
                                  "fp32": 1000.0 / (proj_ms + bin_ms + fwd32)},
             "train_step_ms_fp32": proj_ms + bin_ms + fwd32 + bwd_ms + pbwd_ms,
@@ -419,11 +424,13 @@ def bench_large(dev, flush, steps=5, warmup=2):
     shared = [_events_ms(lambda: r.project(d), steps, warmup, flush),
               _events_ms(lambda: r.bin_sort(), steps, warmup, flush)]
     out["shared_stages_note"] = "project and bin_sort timed once (identical for both renderers)"
-    for prec in ("tc_fp16_split", "fp32"):
+    for prec in ("tc_fp16_split", "fp32", "fp32_frag2mat"):
         stg = shared + [_events_ms(lambda: r.render(d["opacity"], prec), steps, warmup, flush)]
         out[prec] = {"stages_ms": dict(zip(["project", "bin_sort", "render_fwd"], stg)), "frame_ms": sum(stg),
                      "frames_per_s": 1000.0 / sum(stg)}
     out["speedup_render"] = out["fp32"]["stages_ms"]["render_fwd"] / out["tc_fp16_split"]["stages_ms"]["render_fwd"]
+    out["speedup_render_vs_fp32_same_skip"] = (out["fp32_frag2mat"]["stages_ms"]["render_fwd"] /
+                                               out["tc_fp16_split"]["stages_ms"]["render_fwd"])
     out["speedup_frame"] = out["fp32"]["frame_ms"] / out["tc_fp16_split"]["frame_ms"]
     r.render(d["opacity"], "fp32")
     gimg = torch.ones_like(r.out["img"])
@@ -460,6 +467,10 @@ ABLATION = [
     # (label, precision, early_cull, tile_cull): Table 4 (EarlyCull x Frag2Mat with G2L) ...
     ("fp32", "fp32", False, True),
     ("fp32+earlycull", "fp32", True, True),
+    # the tensor-core renderer with its product u^T v on CUDA cores in FP32: the same schedule, staging,
+    # block marks and EarlyCull, so against the rows below only the tensor-core product differs
+    ("fp32_frag2mat_g2l+earlycull", "fp32_frag2mat", True, False),
+    ("fp32_frag2mat_g2l+earlycull+block_marks", "fp32_frag2mat", True, True),
     ("frag2mat_g2l_fp16", "tc_fp16", False, False),
     ("frag2mat_g2l_fp16+earlycull", "tc_fp16", True, False),
     ("frag2mat_g2l_fp16+earlycull+block_marks", "tc_fp16", True, True),
@@ -483,7 +494,8 @@ def bench_ablation(r, dsc, flush, img32, oracle_img=None, mask=None, reps=10, wa
         fn()
         torch.cuda.synchronize()
         im = r.out["img"].cpu().numpy().astype(np.float64)
-        row = {"precision": prec, "early_cull": ec, "block_marks": tcull and not prec.endswith("_global"),
+        row = {"precision": prec, "early_cull": ec,
+               "block_marks": tcull and prec != "fp32" and not prec.endswith("_global"),
                "render_ms": ms, "finite": bool(np.isfinite(im).all())}
         mse = float(np.mean((im - ref32) ** 2))
         row["psnr_vs_fp32_db"] = 10 * math.log10(1 / mse) if mse > 0 else None
@@ -671,8 +683,10 @@ def run_tcgs(args):
     stream = torch.cuda.current_stream(dev)
 
     use_graph = not args.no_graph
-    # --- FP32 comparison path
+    # --- FP32 comparison paths: the 3DGS baseline kernel, and the tensor-core renderer with its product on
+    # CUDA cores (same schedule, block marks and EarlyCull: only the tensor-core product differs)
     tot32, st32 = time_frames(r, dsc, "fp32", args.steps, args.warmup, use_graph, flush, stream)
+    totcc, stcc = time_frames(r, dsc, "fp32_frag2mat", args.steps, args.warmup, use_graph, flush, stream)
     # --- headline path, with clocks sampled during the timed region; a barrier and a device
     # synchronisation on both sides of it
     barrier_if_distributed()
@@ -865,7 +879,11 @@ def run_tcgs(args):
         "fp32": {"frames_per_s": 1000.0 / ms32, "ms_per_step": ms32,
                  "stages_ms": dict(zip(stage_names, [statistics.mean(s) for s in st32])),
                  "alpha_evals_per_s": alpha_evals / (render32_ms * 1e-3)},
-        "speedup_vs_fp32": {"frame": ms32 / ms * world / world, "render": render32_ms / render_ms},
+        "fp32_same_skip": {"frames_per_s": 1000.0 / statistics.mean(totcc), "ms_per_step": statistics.mean(totcc),
+                           "stages_ms": dict(zip(stage_names, [statistics.mean(s) for s in stcc])),
+                           "kernel": "k_render_tc with the product u^T v on CUDA cores (TCGS_FP32_FRAG2MAT)"},
+        "speedup_vs_fp32": {"frame": ms32 / ms, "render": render32_ms / render_ms,
+                            "render_vs_same_skip": statistics.mean(stcc[2]) / render_ms},
         "accuracy": acc, "status": {"bin_sort": status[0], "render": status[1]},
         "executed_fragment_slots": {"fp32": slots_fp32, "tc": st_tc[2]},
         "roofline": roof, "roofline_all": {"project": rl_proj, "bin_sort": rl_bin, "render_fwd": rl_render},

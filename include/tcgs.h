@@ -68,7 +68,11 @@ typedef enum {
                                coordinates, FP16 inputs in the TC_FP16 layout (overflows to inf past
                                256 px; non-finite exponents are culled).  Every list entry is walked
                                (tile_cull ignored).  tcgs_render_fwd and tcgs_frag2mat_beta only */
-    TCGS_TC_TF32_GLOBAL = 6 /* ablation of Table 5: as TC_FP16_GLOBAL with TF32 inputs */
+    TCGS_TC_TF32_GLOBAL = 6,/* ablation of Table 5: as TC_FP16_GLOBAL with TF32 inputs */
+    TCGS_FP32_FRAG2MAT = 7  /* the tensor-core renderer with its product u^T v (Eq. 18, G2L coefficients
+                               of Eq. 12) evaluated on CUDA cores in FP32: the same persistent schedule,
+                               staging, per-block skip (tile_cull) and EarlyCull, no tensor core.  The
+                               ablation arm that isolates what the tensor-core product buys (Table 4) */
 } tcgs_precision;
 
 /* Pinhole camera.  mean2d = (fx X / Z + cx, fy Y / Z + cy) for camera-space (X, Y, Z). */
@@ -101,7 +105,7 @@ typedef struct {
                                 [6], [7] reserved (0) */
     int32_t* device_status;  /* nullable device int32: set to a tcgs_status on a device-side error */
     const uint32_t* tile_order; /* nullable device [num_tiles]: TC precisions in tile-local coordinates
-                                render with a persistent grid (4 CTAs per SM) that takes the tiles in this
+                                and TCGS_FP32_FRAG2MAT render with a persistent grid (4 CTAs per SM) that takes the tiles in this
                                 order, a permutation of all tiles such as tcgs_tile_order's (the order
                                 changes the schedule, never the image); NULL: one CTA per tile.  A view
                                 of at most tcgs_tc_wave_tiles() tiles is rendered one CTA per tile even
@@ -311,7 +315,8 @@ typedef struct {
  * counter and renders that tile exactly as tcgs_render_fwd does (same per-tile body, so every image
  * is identical to a per-view launch whatever the queue order).  An item is (view << 16) | tile.
  * The order of `queue` decides the schedule only: a longest-predicted-first order shortens the
- * makespan when tile costs are uneven.  TC precisions with G2L only (not the *_GLOBAL ablations).
+ * makespan when tile costs are uneven.  TC precisions with G2L (not the *_GLOBAL ablations) and
+ * TCGS_FP32_FRAG2MAT (the same kernel with the product on CUDA cores).
  * In:  n_views in [1, TCGS_MAX_VIEWS] views (host array of tcgs_view), opacity [P] shared by all
  *      views, bg3 host float[3], queue: device [n_items] uint32.
  * work_counter: device uint32, scratch (reset by the call on `stream`).

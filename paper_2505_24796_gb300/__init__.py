@@ -381,7 +381,7 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
     return out
 
 
-_PERSISTENT_PRECISIONS = ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8")
+_PERSISTENT_PRECISIONS = ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8", "fp32_frag2mat")
 
 
 class Renderer:

@@ -18,9 +18,10 @@ TCGS_OK, TCGS_ERR_INVALID, TCGS_ERR_CUDA, TCGS_ERR_CAPACITY, TCGS_ERR_TIMEOUT, T
 TCGS_ERR_SCRATCH_LIMIT = 6
 TCGS_BIN_SORT_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 (TCGS_FP32, TCGS_TC_FP16, TCGS_TC_FP16_SPLIT, TCGS_TC_FP8, TCGS_TC_TF32, TCGS_TC_FP16_GLOBAL,
- TCGS_TC_TF32_GLOBAL) = range(7)
+ TCGS_TC_TF32_GLOBAL, TCGS_FP32_FRAG2MAT) = range(8)
 PRECISIONS = {"fp32": TCGS_FP32, "tc_fp16": TCGS_TC_FP16, "tc_fp16_split": TCGS_TC_FP16_SPLIT, "tc_fp8": TCGS_TC_FP8,
-              "tc_tf32": TCGS_TC_TF32, "tc_fp16_global": TCGS_TC_FP16_GLOBAL, "tc_tf32_global": TCGS_TC_TF32_GLOBAL}
+              "tc_tf32": TCGS_TC_TF32, "tc_fp16_global": TCGS_TC_FP16_GLOBAL, "tc_tf32_global": TCGS_TC_TF32_GLOBAL,
+              "fp32_frag2mat": TCGS_FP32_FRAG2MAT}
 
 
 class tcgs_camera(ctypes.Structure):

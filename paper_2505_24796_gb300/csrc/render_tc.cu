@@ -39,6 +39,7 @@
 #include <cuda_fp8.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -54,6 +55,7 @@ constexpr int kPBytes = kN * 48;       // one parameter buffer: 3 float4 per slo
 constexpr int kSmemA = 0;              // U: 256 x 16 f16 = 8192 B (two 128-row halves)
 constexpr int kSmemB = 8192;           // V: 3 buffers
 constexpr int kSmemP = kSmemB + 3 * kVBytes;   // slot parameters and colours: 3 buffers
+constexpr int kSmemVf = kSmemP + 3 * kPBytes;  // CUDA-core product: FP32 v of each slot, 3 buffers of kN x 32 B
 // 46 KB of dynamic shared memory caps residency at 4 CTAs per SM (4 x 47 KB <= 228 KB < 5 x 47 KB),
 // so 4 x 128 TMEM columns always fit in the 512 available and tcgen05.alloc never waits; the
 // launch bound (56 registers a thread) lets all 4 be resident
@@ -237,6 +239,7 @@ struct TcParams {
     float alpha_max;
     int enc;                    // operand encoding (kEnc*)
     int global;                 // 1: Frag2Mat in global pixel coordinates (ablation, no G2L)
+    int cuda_core;              // 1: the product u^T v on CUDA cores in FP32 (TCGS_FP32_FRAG2MAT)
     int tile_cull;
     int early_cull;             // selects the kernel instance (kEarly)
     int32_t* status;
@@ -274,10 +277,16 @@ __device__ __forceinline__ Slot load_slot(const ViewData& vd, const float* opaci
     return d;
 }
 
-// kEarly: EarlyCull form of the cull test; kSplit: the default encoding (TC_FP16_SPLIT with G2L)
-// fixed at compile time, otherwise the encoding and frame come from p.
-template <bool kInspect, bool kStats, bool kQueue, bool kEarly, bool kSplit>
+// Product paths: the tensor cores with the encoding and frame taken from p (kPathGeneric), the tensor
+// cores with the default encoding fixed at compile time (TC_FP16_SPLIT with G2L), or the same product
+// u^T v on CUDA cores in FP32 (TCGS_FP32_FRAG2MAT: no TMEM, no MMA; everything else identical).
+enum : int { kPathGeneric = 0, kPathSplit = 1, kPathCudaCore = 2 };
+
+// kEarly: EarlyCull form of the cull test; kPath: how the exponents are produced (above).
+template <bool kInspect, bool kStats, bool kQueue, bool kEarly, int kPath>
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams p) {
+    constexpr bool kSplit = kPath == kPathSplit;
+    constexpr bool kCC = kPath == kPathCudaCore;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
@@ -298,19 +307,25 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     uint8_t* sA = smem + kSmemA;
     const uint32_t mbar0 = smem_u32(&s_mbar[0]);
     const int enc = kSplit ? (int)kEncF16Split : p.enc;
-    const bool global = kSplit ? false : p.global != 0;
+    const bool global = (kSplit || kCC) ? false : p.global != 0;
+    // CUDA-core product: this thread's tile-local pixel vector (u1..u5; u0 = 1) in registers
+    const float ux = (float)lx + 0.5f - kTile / 2, uy = (float)ly + 0.5f - kTile / 2;
+    const float uxx = ux * ux, uxy = ux * uy, uyy = uy * uy;
 
     if (producer) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (!kCC) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&s_tmem)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
         if (lane == 0) {
             mbar_init(mbar0, 1);
             mbar_init(mbar0 + 8, 1);
             s_timeout = 0;
         }
-    } else {
+    } else if (!kCC) {
         // U row t = this thread's pixel, tile-local (G2L: dp = p - p(T)); the same for every tile.
         // Without G2L (one tile per CTA) it is the global pixel centre of the CTA's tile.
         float dx = (float)lx + 0.5f - kTile / 2, dy = (float)ly + 0.5f - kTile / 2;
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     __syncthreads();   // U visible to the tensor core, TMEM address and mbarriers published
     tc_fence_after();
     pdl_wait();        // the set-up above touches no global memory; the tiles below do
-    const uint32_t tmem = s_tmem;
+    const uint32_t tmem = kCC ? 0u : s_tmem;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const float kInf = __int_as_float(0x7f800000);
     uint32_t phase_bits = 0;   // producer lane 0: completed-phase parity of the two mbarriers
@@ -427,6 +442,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
             sP[3 * lane] = make_float4(mx, my, d.s11, d.s12);
             sP[3 * lane + 1] = make_float4(d.s22, lim, ia, ic);
             sP[3 * lane + 2] = make_float4(d.r, d.g, d.b, 0.f);
+            if (kCC) {   // FP32 coefficients for the CUDA-core product; no FP16 operand
+                float4* sV = reinterpret_cast<float4*>(smem + kSmemVf + buf * (kN * 32));
+                sV[2 * lane] = make_float4(v[0], v[1], v[2], v[3]);
+                sV[2 * lane + 1] = make_float4(v[4], v[5], 0.f, 0.f);
+                return;
+            }
             if (!global) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) v[k] = fminf(65504.f, fmaxf(-65504.f, v[k]));   // FP16-finite
@@ -447,6 +468,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
         };
         // Producer lane 0: both 128-row halves of U against the same V, committed to one mbarrier.
         auto issue_mma = [&](uint32_t k) {
+            if (kCC) return;
             tc_fence_after();
             const int vb = (int)(k % 3u), tb = (int)(k & 1u);
             const uint64_t descB = make_desc(smem_u32(smem + kSmemB + vb * kVBytes));
@@ -478,6 +500,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                          : "memory");
         };
         auto wait_mma = [&](uint32_t k) -> bool {   // producer lane 0, batches in order
+            if (kCC) return true;
             const uint32_t tb = k & 1u;
             const bool ok = mbar_wait(mbar0 + 8u * tb, (phase_bits >> tb) & 1u);
             phase_bits ^= 1u << tb;
@@ -560,8 +583,15 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 while (m) {
                     const int j = __ffs(m) - 1;
                     m &= m - 1;
-                    const float b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
-                    tmem_wait_ld();
+                    float b2;
+                    if (kCC) {   // u^T v on CUDA cores, FP32 (broadcast shared-memory reads)
+                        const float4* sV = reinterpret_cast<const float4*>(smem + kSmemVf + (k % 3u) * (kN * 32));
+                        const float4 va = sV[2 * j], vb = sV[2 * j + 1];
+                        b2 = fmaf(vb.y, uyy, fmaf(vb.x, uxy, fmaf(va.w, uxx, fmaf(va.z, uy, fmaf(va.y, ux, va.x)))));
+                    } else {
+                        b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
+                        tmem_wait_ld();
+                    }
                     const float e = ex2_approx(b2);
                     // EarlyCull compares log2(alpha) with -log2(255); without it alpha itself is
                     // compared with 1/255 (thr is infinite once the pixel has terminated)
@@ -646,7 +676,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     (void)stopped;
     tc_fence_before();
     __syncthreads();
-    if (producer) {
+    if (producer && !kCC) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
@@ -674,32 +704,32 @@ __global__ void k_wait_selftest(int32_t* status, uint32_t polls) {
     if (threadIdx.x == 0 && !mbar_wait(a, 0u, polls)) set_status(status, TCGS_ERR_TIMEOUT);
 }
 
-int g_checked_device = -1;
-bool g_device_ok = false;
-int g_sm_count = 0;
-
-bool device_is_sm103() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (dev == g_checked_device) return g_device_ok;
-    int major = 0, minor = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    g_checked_device = dev;
-    g_device_ok = (major == 10 && minor == 3);
-    return g_device_ok;
+// The current device when it is an sm_103 part (sms = its SM count), else false.
+bool device_is_sm103(int* sms = nullptr) {
+    DeviceInfo d;
+    if (!current_device_info(&d) || !d.sm103) return false;
+    if (sms) *sms = d.sms;
+    return true;
 }
 
-bool g_attr_set[2][2][2][2][2] = {};
+// Whether the dynamic shared memory size has been raised for an instance on a device (one bit per
+// instance; function attributes are per device).
+std::mutex g_attr_mutex;
+uint64_t g_attr_set[kMaxDevices] = {};
 
-template <bool kInspect, bool kStats, bool kQueue, bool kEarly, bool kSplit>
+template <bool kInspect, bool kStats, bool kQueue, bool kEarly, int kPath>
 tcgs_status launch_tc_t(const TcParams& p, int blocks, cudaStream_t s) {
-    auto kern = k_render_tc<kInspect, kStats, kQueue, kEarly, kSplit>;
-    if (!g_attr_set[kInspect][kStats][kQueue][kEarly][kSplit]) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
-            return TCGS_ERR_CUDA;
-        g_attr_set[kInspect][kStats][kQueue][kEarly][kSplit] = true;
+    auto kern = k_render_tc<kInspect, kStats, kQueue, kEarly, kPath>;
+    DeviceInfo d;
+    if (!current_device_info(&d)) return TCGS_ERR_CUDA;
+    const uint64_t bit = 1ull << (32 * kInspect + 16 * kStats + 8 * kQueue + 4 * kEarly + kPath);
+    {
+        std::lock_guard<std::mutex> lock(g_attr_mutex);
+        if (!(g_attr_set[d.device] & bit)) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
+                return TCGS_ERR_CUDA;
+            g_attr_set[d.device] |= bit;
+        }
     }
     launch_pdl(kern, blocks, kTcThreads, kSmemDyn, s, p);
     count_launches(1);
@@ -709,16 +739,20 @@ tcgs_status launch_tc_t(const TcParams& p, int blocks, cudaStream_t s) {
 
 // The cull test and the operand encoding sit in the per-fragment and per-batch paths, so the
 // default configuration (EarlyCull, split encoding, G2L) is an instance of its own; the other
-// encodings and the alpha-form cull test share generic instances.
+// encodings and the alpha-form cull test share generic instances.  The CUDA-core product has
+// instances of its own, with and without EarlyCull.
 template <bool kInspect, bool kStats, bool kQueue>
 tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
     if constexpr (kInspect) {
-        return launch_tc_t<kInspect, kStats, kQueue, true, false>(p, blocks, s);
+        return launch_tc_t<kInspect, kStats, kQueue, true, kPathGeneric>(p, blocks, s);
     } else {
+        if (p.cuda_core)
+            return p.early_cull ? launch_tc_t<kInspect, kStats, kQueue, true, kPathCudaCore>(p, blocks, s)
+                                : launch_tc_t<kInspect, kStats, kQueue, false, kPathCudaCore>(p, blocks, s);
         const bool split = p.enc == kEncF16Split && !p.global;
-        if (!p.early_cull) return launch_tc_t<kInspect, kStats, kQueue, false, false>(p, blocks, s);
-        if (split) return launch_tc_t<kInspect, kStats, kQueue, true, true>(p, blocks, s);
-        return launch_tc_t<kInspect, kStats, kQueue, true, false>(p, blocks, s);
+        if (!p.early_cull) return launch_tc_t<kInspect, kStats, kQueue, false, kPathGeneric>(p, blocks, s);
+        if (split) return launch_tc_t<kInspect, kStats, kQueue, true, kPathSplit>(p, blocks, s);
+        return launch_tc_t<kInspect, kStats, kQueue, true, kPathGeneric>(p, blocks, s);
     }
 }
 
@@ -737,6 +771,10 @@ bool is_tc_precision(int precision) {
            precision == TCGS_TC_TF32 || precision == TCGS_TC_FP16_GLOBAL || precision == TCGS_TC_TF32_GLOBAL;
 }
 
+// Precisions rendered by k_render_tc (per view or batched): the tensor-core ones and the same
+// kernel with the product on CUDA cores.
+bool uses_tile_kernel(int precision) { return is_tc_precision(precision) || precision == TCGS_FP32_FRAG2MAT; }
+
 bool is_global_precision(int precision) {
     return precision == TCGS_TC_FP16_GLOBAL || precision == TCGS_TC_TF32_GLOBAL;
 }
@@ -753,6 +791,7 @@ TcParams base_params(int precision, const float* opacity) {
         default: p.enc = kEncF16Pad; break;   // TC_FP16, TC_FP16_GLOBAL
     }
     p.global = is_global_precision(precision) ? 1 : 0;
+    p.cuda_core = precision == TCGS_FP32_FRAG2MAT ? 1 : 0;
     p.alpha_max = 0.99f;
     p.tile_cull = 1;
     p.early_cull = 1;
@@ -765,7 +804,8 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
                              const uint32_t* ids_sorted, const float* mean2d, const float* conic,
                              const float* opacity, const float* rgb, const float* bg3, float* img, float* T_final,
                              uint32_t* n_contrib, cudaStream_t s) {
-    if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;
+    int sms = 0;
+    if (!device_is_sm103(&sms)) return TCGS_ERR_UNSUPPORTED;
     TcParams p = base_params(opts->precision, opacity);
     p.v[0] = make_view(cam, tile_ranges, ids_sorted, mean2d, conic, rgb, img, T_final, n_contrib, opts->tile_stats);
     p.n_views = 1;
@@ -776,7 +816,7 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
     p.early_cull = opts->early_cull;
     const int tiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
     if (opts->tile_order && !opts->work_counter) return TCGS_ERR_INVALID;
-    if (opts->tile_order && !p.global && tiles > g_sm_count * kTcCtasPerSm) {
+    if (opts->tile_order && !p.global && tiles > sms * kTcCtasPerSm) {
         // persistent grid over the tiles in the given order: each CTA allocates TMEM and builds U
         // once, and the longest lists start first (with at most one wave of tiles every tile starts
         // at once, so the plain grid below runs without the counter's reset)
@@ -785,7 +825,7 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
         p.n_items = (uint32_t)tiles;
         p.counter = opts->work_counter;
         zero_counter(opts->work_counter, s);
-        int ctas = g_sm_count * kTcCtasPerSm;
+        int ctas = sms * kTcCtasPerSm;
         if (ctas > tiles) ctas = tiles;
         return opts->tile_stats ? launch_tc<false, true, true>(p, ctas, s) : launch_tc<false, false, true>(p, ctas, s);
     }
@@ -822,6 +862,7 @@ extern "C" tcgs_status tcgs_render_fwd(const tcgs_camera* cam, const tcgs_render
         case TCGS_TC_TF32:
         case TCGS_TC_FP16_GLOBAL:
         case TCGS_TC_TF32_GLOBAL:
+        case TCGS_FP32_FRAG2MAT:
             return launch_render_tc(cam, opts, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, bg3, img,
                                     T_final, n_contrib, s);
         default:
@@ -837,7 +878,7 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     if (n_views < 1 || n_views > TCGS_MAX_VIEWS || !views || !opts || !opacity || n_items < 0 ||
         (n_items > 0 && (!queue || !work_counter)))
         return TCGS_ERR_INVALID;
-    if (!is_tc_precision(opts->precision) || is_global_precision(opts->precision)) return TCGS_ERR_INVALID;
+    if (!uses_tile_kernel(opts->precision) || is_global_precision(opts->precision)) return TCGS_ERR_INVALID;
     if (!(opts->alpha_max > 0.f && opts->alpha_max <= 1.f)) return TCGS_ERR_INVALID;
     TcParams p = base_params(opts->precision, opacity);
     for (int v = 0; v < n_views; ++v) {
@@ -852,7 +893,8 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     }
     p.n_views = n_views;
     if (n_items == 0) return TCGS_OK;
-    if (!device_is_sm103()) return TCGS_ERR_UNSUPPORTED;
+    int sms = 0;
+    if (!device_is_sm103(&sms)) return TCGS_ERR_UNSUPPORTED;
     for (int i = 0; i < 3; ++i) p.bg[i] = bg3 ? bg3[i] : 0.f;
     p.alpha_max = opts->alpha_max;
     p.status = opts->device_status;
@@ -866,7 +908,7 @@ extern "C" tcgs_status tcgs_render_fwd_batched(int32_t n_views, const tcgs_view*
     bool any_stats = false;
     for (int v = 0; v < n_views; ++v) any_stats = any_stats || views[v].tile_stats;
     // persistent grid: at most the CTAs that are resident at once (4 per SM for this kernel)
-    int ctas = g_sm_count * kTcCtasPerSm;
+    int ctas = sms * kTcCtasPerSm;
     if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
     if (ctas > n_items) ctas = n_items;
     return any_stats ? launch_tc<false, true, true>(p, ctas, s) : launch_tc<false, false, true>(p, ctas, s);
@@ -895,7 +937,8 @@ extern "C" tcgs_status tcgs_frag2mat_beta(const tcgs_camera* cam, int32_t precis
 
 extern "C" int32_t tcgs_tc_wave_tiles(void) {
     using namespace tcgs;
-    return device_is_sm103() ? g_sm_count * kTcCtasPerSm : 0;
+    int sms = 0;
+    return device_is_sm103(&sms) ? sms * kTcCtasPerSm : 0;
 }
 
 extern "C" tcgs_status tcgs_selftest_bounded_wait(int32_t* device_status, uint32_t polls, tcgs_stream stream) {
