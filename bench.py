@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--diff-frames", action="store_true",
                     help="profiling run: two forward + backward frames of the differentiation workload, stage "
                          "times per frame (no headline line)")
+    ap.add_argument("--render-arms", action="store_true",
+                    help="profiling run: the headline frame binned once, then rendered twice by each renderer arm "
+                         "(TC split, the same kernel with the product on CUDA cores, the 3DGS-style FP32 kernel); "
+                         "render times per arm (no headline line)")
     ap.add_argument("--coverage", default="exact", choices=["exact", "square"],
                     help="tile coverage of the headline binning: the 3-sigma square of the paper's pipeline, or "
                          "exact (tcgs_bin_sort_exact); the other one is timed beside it")
@@ -979,6 +983,32 @@ def run_diff_frames(args):
               flush=True)
 
 
+def run_render_arms(args):
+    """The headline frame (exact tile coverage), projected and binned once, then rendered twice by each
+    renderer arm in turn: the small case for ncu captures comparing the arms' kernels."""
+    import torch
+    import paper_2505_24796_gb300 as tc
+    cam, sc = workload(args.scale)
+    d = tc.scene_to_device(sc, "cuda")
+    pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
+    n = int(pr["tiles_touched"].to(torch.int64).sum().item())
+    del pr
+    r = tc.Renderer(cam, len(sc["opacity"]), n + 1024, device="cuda", exact_tiles=args.coverage == "exact")
+    r.project(d)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    for rep in range(2):
+        ms = {}
+        for prec in ("tc_fp16_split", "fp32_frag2mat", "fp32"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r.render(d["opacity"], prec)
+            e1.record()
+            e1.synchronize()
+            ms[prec] = e0.elapsed_time(e1)
+        print(json.dumps({"render_arms": rep, "splats": int(r.bins["n_splats"].item()), "ms": ms}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -987,6 +1017,8 @@ def main():
         run_large_frames(args)
     elif args.diff_frames:
         run_diff_frames(args)
+    elif args.render_arms:
+        run_render_arms(args)
     else:
         run_tcgs(args)
 

@@ -118,7 +118,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint32
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// tcgen05.wait::ld with the registers of the loads it completes as operands, so that no use of them
+// can be scheduled above the wait.
+__device__ __forceinline__ void tmem_wait_ld1(uint32_t& a) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a)::"memory");
+}
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+}
 
 __device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
     uint32_t r;
@@ -564,7 +576,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 const uint32_t taddr = tmem + lane_base + (uint32_t)((k & 1u) * 2 * kN + half * kN);
                 uint32_t r[32];
                 tmem_ld32(taddr, r);
-                tmem_wait_ld();
+                tmem_wait_ld32(r);
                 const uint32_t b0 = start + k * kN;
                 const uint32_t nb = stop - b0 < (uint32_t)kN ? stop - b0 : (uint32_t)kN;
                 const int pix = ly * kTile + lx;
@@ -589,8 +601,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                         const float4 va = sV[2 * j], vb = sV[2 * j + 1];
                         b2 = fmaf(vb.y, uyy, fmaf(vb.x, uxy, fmaf(va.w, uxx, fmaf(va.z, uy, fmaf(va.y, ux, va.x)))));
                     } else {
-                        b2 = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
-                        tmem_wait_ld();
+                        uint32_t r = tmem_ld1(taddr + (uint32_t)j);
+                        tmem_wait_ld1(r);
+                        b2 = __uint_as_float(r);
                     }
                     const float e = ex2_approx(b2);
                     // EarlyCull compares log2(alpha) with -log2(255); without it alpha itself is
