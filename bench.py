@@ -347,21 +347,20 @@ def bench_differentiation(dev, flush):
             "bwd_alpha_evals_per_s": (st[0] + st[1]) / (bwd_ms * 1e-3)}
 
 
-def bench_scheduler(dev, train_views=200, chunk=16):
-    """16 views of one 3M-Gaussian scene at uneven resolutions: the MLP is trained on the tile costs
-    recorded by `train_views` renders of other views, then orders the batched renderer's queue."""
+def _sched_run(dev, eval_cams, scene, train_cams, label, chunk=16):
+    """Train the tile-cost MLP on the tile costs recorded by renders of train_cams, then time the
+    batched render of eval_cams in natural, list-length and MLP order; also the FP32 arms of the same
+    batch: the batched renderer with its product on CUDA cores (list-length order) and the 3DGS-style
+    FP32 kernel launched view by view."""
     import torch
     import paper_2505_24796_gb300 as tc
     from oracle import sched as osc
-    from paper_2505_24796_gb300 import scenes
     from paper_2505_24796_gb300.sched import MultiView, TileCostModel
-    eval_cams, scene = scenes.learned_scheduler()
     d = tc.scene_to_device(scene, dev)
     t0 = time.perf_counter()
     Xs, ys = [], []
-    cams = scenes.multiview_cameras(train_views, 77)
-    for i in range(0, train_views, chunk):
-        mv = MultiView(d, cams[i:i + chunk], device=dev)
+    for i in range(0, len(train_cams), chunk):
+        mv = MultiView(d, train_cams[i:i + chunk], device=dev)
         X, y = mv.training_data()
         Xs.append(X); ys.append(y)
         del mv
@@ -381,28 +380,68 @@ def bench_scheduler(dev, train_views=200, chunk=16):
     nlen = torch.cat([(r.bins["tile_ranges"][:, 1] - r.bins["tile_ranges"][:, 0]) for r in mv.views]).cpu().numpy()
     A = np.c_[np.log1p(nlen), np.ones_like(ytn)]
     base = A @ np.linalg.lstsq(A, ytn, rcond=None)[0]
-    res = {"workload": "learned scheduler: 16 views (640x480..1920x1080, cameras on a sphere of radius 20) of a "
-                       "3M-Gaussian scene; MLP 8->32->32->1 trained on tile costs of %d other renders" % train_views,
-           "tiles": int(Xt.shape[0]), "train_items": int(X.shape[0]), "train_loss": loss,
+    res = {"workload": label, "tiles": int(Xt.shape[0]), "train_items": int(X.shape[0]), "train_loss": loss,
            "collect_s": collect_s, "train_s": train_s,
-           "heldout_mse_log_cost": {"mlp": float(np.mean((pn - ytn) ** 2)), "list_length_fit": float(np.mean((base - ytn) ** 2))}}
+           "heldout_mse_log_cost": {"mlp": float(np.mean((pn - ytn) ** 2)),
+                                    "list_length_fit": float(np.mean((base - ytn) ** 2))}}
     items = mv.items().cpu().numpy()
     cyc = dict(zip(items.tolist(), cycles.cpu().numpy().tolist()))
-    workers = 152 * 4   # resident CTAs of the persistent renderer
-    times, sim = {}, {}
+    workers = tc.tcgs_tc_wave_tiles()   # resident CTAs of the persistent renderer
+    times, sim, imgs = {}, {}, {}
     for policy in ("natural", "length", "mlp"):
         q = mv.queue(policy, model)
-        times[policy] = mv.time_render(q, reps=10, warmup=3)
+        times[policy] = mv.time_render(q, reps=15, warmup=3)
         sim[policy] = osc.lpt_makespan([cyc[i] for i in q.cpu().numpy().tolist()], workers)
+        torch.cuda.synchronize()
+        imgs[policy] = [r.out["img"].clone() for r in mv.views]
     res["batched_render_ms"] = times
     res["simulated_makespan_cycles"] = sim
     cyc_all = np.asarray(list(cyc.values()), dtype=np.float64)
     # no order of whole tiles can finish before the heaviest tile, nor before the work spread evenly
     res["makespan_lower_bound_cycles"] = {"heaviest_tile": float(cyc_all.max()),
                                           "even_spread": float(cyc_all.sum() / workers)}
+    res["resident_ctas"] = workers
     res["gain_vs_length"] = times["length"] / times["mlp"]
     res["gain_vs_natural"] = times["natural"] / times["mlp"]
+    res["simulated_gain_vs_length"] = sim["length"] / sim["mlp"]
+    res["images_equal_across_orders"] = all(torch.equal(a, b) for p in ("natural", "length")
+                                            for a, b in zip(imgs[p], imgs["mlp"]))
+    # FP32 arms of the same batch
+    q_len = mv.queue("length")
+    mv_cc = MultiView(d, eval_cams, precision="fp32_frag2mat", device=dev)
+    t_cc = mv_cc.time_render(q_len, reps=15, warmup=3)
+    del mv_cc
+
+    opts32 = tc.render_opts("fp32")
+
+    def per_view_fp32():
+        for r in mv.views:
+            tc.tcgs_render_fwd(r.cam, opts32, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"],
+                               r.proj["conic"], d["opacity"], r.proj["rgb"], out=r.out)
+    t_fp32 = _events_ms(per_view_fp32, 15, 3)
+    res["fp32_arms_ms"] = {"batched_same_skip_length_order": t_cc, "fp32_3dgs_kernel_view_by_view": t_fp32}
+    res["speedup_tc_mlp_vs_fp32"] = {"vs_same_skip_batched": t_cc / times["mlp"], "vs_fp32_view_by_view": t_fp32 / times["mlp"]}
     return res
+
+
+def bench_scheduler(dev, train_views=200):
+    """Config 4: 16 views of one 3M-Gaussian scene at uneven resolutions; the MLP is trained on the tile
+    costs recorded by train_views renders of other views, then orders the batched renderer's queue."""
+    from paper_2505_24796_gb300 import scenes
+    eval_cams, scene = scenes.learned_scheduler()
+    return _sched_run(dev, eval_cams, scene, scenes.multiview_cameras(train_views, 77),
+                      "learned scheduler: 16 views (640x480..1920x1080, cameras on a sphere of radius 20) of a "
+                      "3M-Gaussian scene; MLP 8->32->32->1 trained on tile costs of %d other renders" % train_views)
+
+
+def bench_scheduler_occluded(dev, train_views=200):
+    """16 views at 320x240 (about 8 tiles per resident CTA) of a faint volume with opaque clusters, where
+    list length mispredicts tile cost; the MLP is trained on train_views other renders."""
+    from paper_2505_24796_gb300 import scenes
+    eval_cams, scene = scenes.learned_scheduler_occluded()
+    return _sched_run(dev, eval_cams, scene, scenes.low_res_cameras(train_views, 77),
+                      "learned scheduler, occluded volume: 16 views at 320x240 of a faint volume (200k Gaussians) "
+                      "with 60 opaque clusters (180k); MLP trained on tile costs of %d other renders" % train_views)
 
 
 def bench_large(dev, flush, steps=5, warmup=2):
@@ -861,6 +900,7 @@ def run_tcgs(args):
         for name, fn in (("plain", lambda: bench_plain(dev, flush, stream)),
                          ("differentiation", lambda: bench_differentiation(dev, flush)),
                          ("scheduler", lambda: bench_scheduler(dev, args.sched_train_views)),
+                         ("scheduler_occluded", lambda: bench_scheduler_occluded(dev, args.sched_train_views)),
                          ("large", lambda: bench_large(dev, flush))):
             try:
                 extras[name] = fn()

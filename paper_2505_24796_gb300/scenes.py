@@ -174,6 +174,44 @@ def multiview_cameras(n_views, seed, radius=20.0):
     return cams
 
 
+def occluded_volume(n_faint=200_000, n_blobs=60, per_blob=3000, seed=6, radius=6.0, blob_radius=2.0):
+    """Scheduler workload where list length mispredicts tile cost: a faint volume (means uniform in a
+    ball of the given radius around the scene centre, opacity sigmoid(N(-3, 0.5)): long lists that
+    rarely terminate) with n_blobs opaque clusters inside it (per_blob Gaussians each, normal with
+    standard deviation blob_radius / 2 around centres uniform in a cube of half-width 0.7 radius,
+    opacity sigmoid(N(4, 1)): they lengthen the lists of the tiles they cover but end those tiles'
+    blending early).  Log-scales N(-2.3, 0.3) per axis, uniform rotations, SH degree 0."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n_faint, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    mf = SCENE_CENTRE + u * (radius * rng.random(n_faint) ** (1.0 / 3.0))[:, None]
+    centres = SCENE_CENTRE + rng.uniform(-0.7 * radius, 0.7 * radius, (n_blobs, 3))
+    labels = rng.integers(0, n_blobs, n_blobs * per_blob)
+    mb = centres[labels] + rng.standard_normal((n_blobs * per_blob, 3)) * (blob_radius / 2.0)
+    means = np.r_[mf, mb]
+    P = len(means)
+    scales = np.exp(rng.normal(-2.3, 0.3, (P, 3)))
+    quats = _quats(rng, P)
+    opacity = np.r_[_sigmoid(rng.normal(-3.0, 0.5, n_faint)), _sigmoid(rng.normal(4.0, 1.0, n_blobs * per_blob))]
+    return _pack(means, scales, quats, opacity, _sh(rng, P, 0, 0.0), 0)
+
+
+def low_res_cameras(n_views, seed, width=320, height=240, radius=20.0):
+    """Cameras as multiview_cameras (on a sphere around the scene centre, looking at it) at one fixed
+    low resolution, fx = fy = width."""
+    cams = multiview_cameras(n_views, seed, radius)
+    for c in cams:
+        vm = c["viewmat"]
+        c.update(pinhole(width, height, float(width), viewmat=vm, campos=c["campos"]))
+    return cams
+
+
+def learned_scheduler_occluded(n_views=16, seed=6):
+    """Scheduler workload with few, uneven items per resident CTA: 16 views at 320x240 (4,800 tiles) of
+    the occluded volume (380k Gaussians)."""
+    return low_res_cameras(n_views, seed + 1000), occluded_volume(seed=seed)
+
+
 def learned_scheduler(P=3_000_000, n_views=16, seed=4):
     """Learned scheduler: 16 views of one 3M-Gaussian scene (plain-workload distributions)."""
     rng = np.random.default_rng(seed)
