@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ 
 // Stable scatter of one 8-bit digit.  Per tile of kThreads x KI keys: warp-level ranks
 // (__match_any_sync), a per-digit prefix over the warps, keys and values regrouped by digit in
 // shared memory, then written out so that consecutive threads write consecutive addresses of each
-// digit's run (coalesced).  Keys of the next tile are loaded one tile ahead; values are loaded once
-// the keys are ranked.
+// digit's run (coalesced).  Keys of the next tile are loaded one tile ahead; a tile's values are
+// requested before its keys are ranked.
 template <int KI>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
@@ -165,9 +165,15 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     for (uint32_t tile = lo; tile < hi; tile += TI) {
         const uint32_t tile_n = hi - tile < (uint32_t)TI ? hi - tile : (uint32_t)TI;
         const uint32_t base = tile + (uint32_t)warp * (32 * KI);
-        uint32_t k[KI], pos[KI];
+        uint32_t k[KI], pos[KI], v[KI];
 #pragma unroll
         for (int r = 0; r < KI; ++r) k[r] = kn[r];
+        // this tile's values, requested now so that the loads are in flight during the ranking
+#pragma unroll
+        for (int r = 0; r < KI; ++r) {
+            const uint32_t i = base + r * 32 + lane;
+            v[r] = i < hi ? vals_in[i] : 0u;
+        }
         if (tile + TI < hi) load_keys(tile + TI);
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) wcnt[w][t] = 0;
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
         }
 #pragma unroll
         for (int r = 0; r < KI; ++r) {
-            if (pos[r] != 0xFFFFFFFFu) sv[pos[r]] = vals_in[base + r * 32 + lane];
+            if (pos[r] != 0xFFFFFFFFu) sv[pos[r]] = v[r];
         }
         __syncthreads();
 #pragma unroll

@@ -628,6 +628,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                     thr = term ? kInf : thr;
                 }
                 done = thr == kInf;   // terminated (thr starts infinite for pixels outside the image)
+                // marks of batch k + 1 (staged in the previous window, so stable during this one) before
+                // the barrier: warps that finish early take this cost while the slowest one walks
+                if (k + 1 < nbat)
+                    mask_cur = __all_sync(0xffffffffu, done) ? 0u : block_mask((int)((k + 1) % 3u));
             }
             walked = (k + 1) * kN;
             tc_fence_before();
@@ -638,11 +642,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 break;
             }
             if (!kInspect && !more) break;
-            if (producer) {
-                if (lane == 0 && k + 2 < nbat) issue_mma(k + 2);
-            } else if (k + 1 < nbat) {
-                mask_cur = __all_sync(0xffffffffu, done) ? 0u : block_mask((int)((k + 1) % 3u));
-            }
+            if (producer && lane == 0 && k + 2 < nbat) issue_mma(k + 2);
         }
         // every MMA issued has been waited for (MMA k + 2 is only issued after the walk of batch k
         // continues, and is waited for in the next window), so TMEM is idle between tiles
