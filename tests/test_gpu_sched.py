@@ -53,11 +53,15 @@ def test_mlp_forward_backward_match_oracle(tc):
     np.testing.assert_allclose(1 / nm[8:], X.astype(np.float64).std(0), rtol=1e-4)
     y = tc.tcgs_mlp_fwd(to_torch(params, DEV), norm, dX).cpu().numpy()
     yr, _ = osc.mlp_forward(params.astype(np.float64), nm, X, fp16=True)
+    # Both sides round every weight, input and activation to FP16; their sums differ (FP32 against
+    # FP64), so an activation near an FP16 rounding boundary can round one ulp apart (2^-11 relative),
+    # which moves the output by about 1e-3 (1 + |y|) at most through these weights.  Measured: max
+    # 9.1e-4, every row within the bound.
     err = np.abs(y - yr)
     close = err <= 2e-3 * (1 + np.abs(yr))
     print(f"\n[mlp fwd] max abs err {err.max():.3e}, 99.9% {np.quantile(err, 0.999):.3e}, rows beyond "
           f"2e-3 (1 + |y|): {int((~close).sum())} of {len(y)}")
-    assert close.mean() >= 0.995 and err.max() < 0.05
+    assert close.all()
     loss = torch.zeros(1, device=DEV)
     grad, _ = tc.tcgs_mlp_bwd(to_torch(params, DEV), norm, dX, to_torch(t, DEV), loss=loss)
     torch.cuda.synchronize()
@@ -66,7 +70,10 @@ def test_mlp_forward_backward_match_oracle(tc):
     ge = np.abs(g - gr)
     print(f"[mlp bwd] max abs err {ge.max():.3e} (max |grad| {np.abs(gr).max():.3e}), max rel err "
           f"{(ge / (np.abs(gr) + 1e-6 * np.abs(gr).max())).max():.3e}")
-    np.testing.assert_allclose(g, gr, rtol=5e-3, atol=2e-3 * np.abs(gr).max())
+    # the backward uses the forward's FP16-rounded values on both sides; the FP32 sums over 3,000 rows
+    # differ from FP64 by about 1e-6 of the largest component (measured 1.1e-6; largest relative
+    # error of a component 6.6e-4)
+    np.testing.assert_allclose(g, gr, rtol=2e-3, atol=1e-5 * np.abs(gr).max())
     assert abs(float(loss.item()) - lr) <= 1e-3 * lr
 
 
