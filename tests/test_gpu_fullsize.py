@@ -188,7 +188,7 @@ def test_large_frame_full_size_matches_oracle_on_sampled_tiles(tc):
     counter = torch.zeros(1, dtype=torch.int32, device=DEV)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     imgs = {}
-    for prec in ("fp32", "tc_fp16_split"):
+    for prec in ("fp32", "tc_fp16_split", "fp32_frag2mat"):
         opts = tc.render_opts(prec, device_status=status, tile_order=order if prec != "fp32" else None,
                               work_counter=counter if prec != "fp32" else None)
         out = tc.tcgs_render_fwd(cam, opts, out_b["tile_ranges"], out_b["ids_sorted"], g["mean2d"], g["conic"],
@@ -208,6 +208,10 @@ def test_large_frame_full_size_matches_oracle_on_sampled_tiles(tc):
     p_tc = psnr(imgtc[:, mask], o["img"][:, mask])
     assert p_tc >= 50.0
     assert (np.abs(imgtc - o["img"]).max(axis=0)[mask] <= 2e-3).mean() >= 0.999
+    # the same kernel with the product on CUDA cores: the TC criteria, and within 1e-4 off the margins
+    imgcc = imgs["fp32_frag2mat"][0]
+    assert psnr(imgcc[:, mask], o["img"][:, mask]) >= 50.0
+    assert np.abs(imgcc - o["img"]).max(axis=0)[keep].max() <= 1e-4
 
     # (2) the whole frame from the scene, as the benchmark renders it
     d = tc.scene_to_device(sc, DEV)

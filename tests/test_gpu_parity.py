@@ -569,7 +569,7 @@ def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
     counter = torch.zeros(1, dtype=torch.int32, device=DEV)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     imgs = {}
-    for prec in ("fp32", "tc_fp16_split", "tc_fp16"):
+    for prec in ("fp32", "tc_fp16_split", "tc_fp16", "fp32_frag2mat"):
         opts = tc.render_opts(prec, device_status=status,
                               tile_order=order if prec != "fp32" else None,
                               work_counter=counter if prec != "fp32" else None)
@@ -593,6 +593,10 @@ def test_full_size_frame_matches_oracle_on_sampled_tiles(tc):
     p16 = psnr(img16[:, mask], o["img"][:, mask])
     w16 = float((np.abs(img16 - o["img"]).max(axis=0)[mask] <= 2e-3).mean())
     assert 50.0 <= p16 <= 60.0 and 0.75 <= w16 <= 0.95, (p16, w16)
+    # the same kernel with the product on CUDA cores: the TC criteria, and within 1e-4 off the margins
+    imgcc = imgs["fp32_frag2mat"][0]
+    assert psnr(imgcc[:, mask], o["img"][:, mask]) >= 50.0
+    assert np.abs(imgcc - o["img"]).max(axis=0)[keep].max() <= 1e-4
 
     # (2) the whole frame from the scene, as the bench renders it
     d = tc.scene_to_device(sc, DEV)
