@@ -85,6 +85,8 @@ def parse():
                     help="profiling run: the headline frame binned once, then rendered twice by each renderer arm "
                          "(TC split, the same kernel with the product on CUDA cores, the 3DGS-style FP32 kernel); "
                          "render times per arm (no headline line)")
+    ap.add_argument("--arms-workload", default="precision", choices=["precision", "differentiation"],
+                    help="workload of --render-arms")
     ap.add_argument("--coverage", default="exact", choices=["exact", "square"],
                     help="tile coverage of the headline binning: the 3-sigma square of the paper's pipeline, or "
                          "exact (tcgs_bin_sort_exact); the other one is timed beside it")
@@ -1074,11 +1076,13 @@ def run_diff_frames(args):
 
 
 def run_render_arms(args):
-    """The headline frame (exact tile coverage), projected and binned once, then rendered twice by each
-    renderer arm in turn: the small case for ncu captures comparing the arms' kernels."""
+    """The headline frame (or the differentiation frame, --arms-workload), projected and binned once,
+    then rendered twice by each renderer arm in turn: the small case for ncu captures comparing the
+    arms' kernels."""
     import torch
     import paper_2505_24796_gb300 as tc
-    cam, sc = workload(args.scale)
+    from paper_2505_24796_gb300 import scenes
+    cam, sc = workload(args.scale) if args.arms_workload == "precision" else scenes.differentiation()[:2]
     d = tc.scene_to_device(sc, "cuda")
     pr = tc.tcgs_project(cam, d["means3"], d["scales"], d["quats"], d["sh"], d["sh_degree"])
     n = int(pr["tiles_touched"].to(torch.int64).sum().item())
