@@ -71,7 +71,8 @@ def test_project_matches_oracle(tc, name, make, tight):
     diff = vis_o != vis_g
     assert diff.mean() < 1e-3, (name, diff.sum())
     both = vis_o & vis_g
-    np.testing.assert_allclose(g["mean2d"][both], pr["mean2d"][both], rtol=2e-6, atol=2e-4)
+    # FP32 rounding of fx X / Z + cx: a few ulps of the coordinate (measured at most 1.5e-5 px)
+    np.testing.assert_allclose(g["mean2d"][both], pr["mean2d"][both], rtol=2e-6, atol=5e-5)
     np.testing.assert_allclose(g["depth"][both], pr["depth"][both], rtol=1e-6)
     scale = np.abs(pr["conic"][both]).max(axis=1)
     cerr = np.abs(g["conic"][both] - pr["conic"][both]).max(axis=1) / scale
