@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 if (kStats) cols += __popc(m);
                 const uint32_t pbase = b0 + 1u - start;   // 1 + list index of column 0
                 while (m) {
-                    const int j = __ffs(m) - 1;
+                    const int j = __clz(__brev(m));   // lowest marked column
                     m &= m - 1;
                     float b2;
                     if (kCC) {   // u^T v on CUDA cores, FP32 (broadcast shared-memory reads)
@@ -614,11 +614,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                     const bool term = pass && (Tn < kTmin);           // Algorithm 1: terminate, unblended
                     const bool blend = pass && !term;
                     const float4 c = sP[3 * j + 2];
-                    const float w = blend ? a * T : 0.f;
+                    // weight alpha T as the drop in transmittance (the weights then telescope to 1 - T)
+                    const float Tb = blend ? Tn : T;
+                    const float w = T - Tb;
                     C0 = fmaf(c.x, w, C0);
                     C1 = fmaf(c.y, w, C1);
                     C2 = fmaf(c.z, w, C2);
-                    T = blend ? Tn : T;
+                    T = Tb;
                     const uint32_t pos = pbase + (uint32_t)j;
                     last = blend ? pos : last;
                     if (kStats) {
