@@ -323,6 +323,7 @@ def bench_differentiation(dev, flush):
     fwd32 = _events_ms(lambda: r.render(d["opacity"], "fp32"), 10, 3, flush)
     fwdtc = _events_ms(lambda: r.render(d["opacity"], "tc_fp16_split"), 10, 3, flush)
     fwdcc = _events_ms(lambda: r.render(d["opacity"], "fp32_frag2mat"), 10, 3, flush)
+    one = _one_pixel_a_thread(r, d, flush, 10, 3)
     r.render(d["opacity"], "fp32")
     bwd_ms = _events_ms(bwd, 10, 3, flush)
     proj_ms = _events_ms(lambda: r.project(d), 10, 3, flush)
@@ -339,6 +340,7 @@ def bench_differentiation(dev, flush):
             "ms": {"project": proj_ms, "bin_sort": bin_ms, "render_fwd_fp32": fwd32,
                    "render_fwd_tc": fwdtc, "render_fwd_fp32_same_skip": fwdcc, "render_bwd": bwd_ms,
                    "project_bwd": pbwd_ms},
+            "pixels_per_thread": r.pixels_per_thread, "render_fwd_one_pixel_a_thread_ms": one,
             "speedup_render": {"vs_fp32": fwd32 / fwdtc, "vs_fp32_same_skip": fwdcc / fwdtc},
             "frames_per_s_fwd": {"tc_fp16_split": 1000.0 / (proj_ms + bin_ms + fwdtc),
                                  "fp32": 1000.0 / (proj_ms + bin_ms + fwd32)},
@@ -477,6 +479,8 @@ def bench_large(dev, flush, steps=5, warmup=2):
     out["speedup_render_vs_fp32_same_skip"] = (out["fp32_frag2mat"]["stages_ms"]["render_fwd"] /
                                                out["tc_fp16_split"]["stages_ms"]["render_fwd"])
     out["speedup_frame"] = out["fp32"]["frame_ms"] / out["tc_fp16_split"]["frame_ms"]
+    out["pixels_per_thread"] = r.pixels_per_thread
+    out["render_fwd_one_pixel_a_thread_ms"] = _one_pixel_a_thread(r, d, flush, steps, warmup)
     r.render(d["opacity"], "fp32")
     gimg = torch.ones_like(r.out["img"])
     P = len(sc["opacity"])
@@ -489,6 +493,17 @@ def bench_large(dev, flush, steps=5, warmup=2):
     del r
     torch.cuda.empty_cache()
     out["square_coverage"] = _coverage_render(cam, d, n + 1024, dev, flush, exact=False, steps=steps, warmup=warmup)
+    return out
+
+
+def _one_pixel_a_thread(r, d, flush, steps, warmup):
+    """Render times of the tile kernel with one pixel a consumer thread (8 x 4 warp blocks), beside the
+    Renderer's own choice (two pixels a thread for views of large footprints); same image."""
+    keep = r.pixels_per_thread
+    r.pixels_per_thread = 1
+    out = {prec: _events_ms(lambda: r.render(d["opacity"], prec), steps, warmup, flush)
+           for prec in ("tc_fp16_split", "fp32_frag2mat")}
+    r.pixels_per_thread = keep
     return out
 
 

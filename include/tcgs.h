@@ -112,6 +112,14 @@ typedef struct {
                                 when an order is given: every tile then starts in the first wave */
     uint32_t* work_counter;  /* device uint32, required with tile_order: the grid's next-tile counter,
                                 zeroed by the call */
+    int32_t pixels_per_thread; /* 0 or 1: the tensor-core renderer's consumer threads blend one pixel
+                                each, its warps own 8x4 blocks (the default); 2: two pixels each, four
+                                rows apart (one in each MMA half, the same TMEM lane), warps owning 8x8
+                                blocks, so every walked list entry serves 64 pixels at the cost of coarser
+                                block marks: faster for views of large footprints, whose batches mark most
+                                entries anyway, slower for views of small ones.  Honoured by
+                                TCGS_TC_FP16_SPLIT and TCGS_FP32_FRAG2MAT with early_cull = 1; the other
+                                configurations render with one.  The image is the same either way */
 } tcgs_render_opts;
 
 /* Human-readable name of a status code (static string). */

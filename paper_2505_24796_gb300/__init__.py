@@ -77,10 +77,12 @@ def _cam(cam) -> tcgs_camera:
 
 
 def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=None, tile_stats=None,
-                device_status=None, tile_cull=True, tile_order=None, work_counter=None) -> tcgs_render_opts:
+                device_status=None, tile_cull=True, tile_order=None, work_counter=None,
+                pixels_per_thread=1) -> tcgs_render_opts:
     """early_cull None: the path's default (off on the FP32 path, the 3DGS baseline; on for the
     tensor-core paths, as the paper's renderer).  tile_order / work_counter: the persistent TC
-    renderer's tile order (tcgs_tile_order) and its counter."""
+    renderer's tile order (tcgs_tile_order) and its counter.  pixels_per_thread: 1, or 2 for views of
+    large footprints (tcgs_render_opts.pixels_per_thread)."""
     o = tcgs_render_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.alpha_max = float(alpha_max)
@@ -90,6 +92,7 @@ def render_opts(precision="tc_fp16_split", alpha_max=0.99, early_cull=None, tile
     o.device_status = _ptr(device_status, torch.int32, "device_status") if device_status is not None else None
     o.tile_order = _ptr(tile_order, torch.int32, "tile_order") if tile_order is not None else None
     o.work_counter = _ptr(work_counter, torch.int32, "work_counter") if work_counter is not None else None
+    o.pixels_per_thread = int(pixels_per_thread)
     return o
 
 
@@ -382,6 +385,9 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
 
 
 _PERSISTENT_PRECISIONS = ("tc_fp16_split", "tc_fp16", "tc_tf32", "tc_fp8", "fp32_frag2mat")
+# A Renderer whose capacity allows at least this many splats per Gaussian renders two pixels a thread
+# (the footprints are large, so the coarser block marks cost little).
+DENSE_SPLATS_PER_GAUSSIAN = 16
 
 
 class Renderer:
@@ -389,19 +395,24 @@ class Renderer:
     project -> bin_sort -> render_fwd on the current stream with no host synchronisation."""
 
     def __init__(self, cam, P: int, capacity: int, device="cuda", stats: bool = False, tight_radius: bool = False,
-                 exact_tiles: bool = True, persistent: bool = True):
+                 exact_tiles: bool = True, persistent: bool = True, pixels_per_thread=None):
         """tight_radius: bin with the opacity-aware coverage square instead of the 3-sigma one.
         exact_tiles (default): keep only the tiles each Gaussian reaches with alpha >= 1/255
         (tcgs_bin_sort_exact: the same images as the rectangle's tiles, shorter lists); False bins
         every tile of the rectangle (tcgs_bin_sort).  persistent (default): the tensor-core renders
         take the tiles longest list first on a persistent grid (tcgs_tile_order) when the view has
         more tiles than one wave of CTAs holds (tcgs_tc_wave_tiles); the image is the same as with
-        one CTA per tile."""
+        one CTA per tile.  pixels_per_thread (tcgs_render_opts.pixels_per_thread): None picks 2 for views
+        of large footprints, where the capacity allows at least DENSE_SPLATS_PER_GAUSSIAN splats per
+        Gaussian, else 1; the image is the same either way."""
         self.cam = _cam(cam)
         self.tight_radius = bool(tight_radius)
         self.exact_tiles = bool(exact_tiles)
         self.opacity = None
         self.P, self.capacity = int(P), int(capacity)
+        if pixels_per_thread is None:
+            pixels_per_thread = 2 if self.capacity >= DENSE_SPLATS_PER_GAUSSIAN * max(self.P, 1) else 1
+        self.pixels_per_thread = int(pixels_per_thread)
         dev = torch.device(device)
         gw, gh = grid(self.cam)
         self.num_tiles = gw * gh
@@ -449,7 +460,8 @@ class Renderer:
         if self.persistent and precision in _PERSISTENT_PRECISIONS and self.num_tiles > self._wave_tiles:
             order = tcgs_tile_order(self.cam, self.bins["tile_ranges"], out=self.tile_order, stream=stream)
         opts = render_opts(precision, alpha_max, early_cull, self.stats, self.device_status, tile_cull,
-                           tile_order=order, work_counter=self.work_counter if order is not None else None)
+                           tile_order=order, work_counter=self.work_counter if order is not None else None,
+                           pixels_per_thread=self.pixels_per_thread)
         return tcgs_render_fwd(self.cam, opts, self.bins["tile_ranges"], self.bins["ids_sorted"],
                                self.proj["mean2d"], self.proj["conic"], opacity, self.proj["rgb"], bg=bg,
                                out=self.out, stream=stream)

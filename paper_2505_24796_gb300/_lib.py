@@ -33,7 +33,7 @@ class tcgs_camera(ctypes.Structure):
 class tcgs_render_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("alpha_max", c_float), ("early_cull", c_int32), ("tile_cull", c_int32),
                 ("tile_stats", c_void_p), ("device_status", c_void_p), ("tile_order", c_void_p),
-                ("work_counter", c_void_p)]
+                ("work_counter", c_void_p), ("pixels_per_thread", c_int32)]
 
 
 TCGS_MAX_VIEWS = 16

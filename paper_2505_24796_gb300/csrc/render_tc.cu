@@ -47,7 +47,6 @@ namespace tcgs {
 namespace {
 
 constexpr int kConsumerWarps = 8;      // 8 warps of 8 x 4 pixels = one 16 x 16 tile, one thread per pixel
-constexpr int kTcThreads = 32 * (kConsumerWarps + 1);   // + one producer warp
 constexpr int kN = 32;                 // Gaussians per MMA batch (UMMA N; slot = producer lane)
 constexpr uint32_t kTmemCols = 4 * kN; // 2 accumulator buffers x 2 row halves
 constexpr int kVBytes = kN * 32;       // one V buffer: 32 x 16 f16
@@ -122,6 +121,9 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 // can be scheduled above the wait.
 __device__ __forceinline__ void tmem_wait_ld1(uint32_t& a) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a)::"memory");
+}
+__device__ __forceinline__ void tmem_wait_ld2(uint32_t& a, uint32_t& b) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a), "+r"(b)::"memory");
 }
 __device__ __forceinline__ void tmem_wait_ld32(uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -254,6 +256,8 @@ struct TcParams {
     int cuda_core;              // 1: the product u^T v on CUDA cores in FP32 (TCGS_FP32_FRAG2MAT)
     int tile_cull;
     int early_cull;             // selects the kernel instance (kEarly)
+    int ppt;                    // pixels per consumer thread (kPPT instance; 2 only for the EarlyCull
+                                // split-FP16 and CUDA-core paths, anything else renders with 1)
     int32_t* status;
     int n_views;
     const uint32_t* queue;      // queue mode: items (view << 16 | tile) in the order to render
@@ -294,11 +298,24 @@ __device__ __forceinline__ Slot load_slot(const ViewData& vd, const float* opaci
 // u^T v on CUDA cores in FP32 (TCGS_FP32_FRAG2MAT: no TMEM, no MMA; everything else identical).
 enum : int { kPathGeneric = 0, kPathSplit = 1, kPathCudaCore = 2 };
 
-// kEarly: EarlyCull form of the cull test; kPath: how the exponents are produced (above).
-template <bool kInspect, bool kStats, bool kQueue, bool kEarly, int kPath>
-__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams p) {
+// Consumer warps and threads of a CTA with kPPT pixels per consumer thread: 8 warps of 8 x 4 pixels
+// (one each), or 4 warps of 8 x 8 pixels (two each, four rows apart: one in each MMA half, at the
+// same TMEM lane), plus the producer warp.
+template <int kPPT>
+constexpr int consumer_warps() { return kPPT == 2 ? 4 : kConsumerWarps; }
+template <int kPPT>
+constexpr int tc_threads() { return 32 * (consumer_warps<kPPT>() + 1); }
+
+// kEarly: EarlyCull form of the cull test; kPath: how the exponents are produced (above); kPPT:
+// pixels per consumer thread (2: coarser 8 x 8 block marks and two blend chains per walked column,
+// which pays off for views of large footprints, whose batches mark most entries anyway).
+template <bool kInspect, bool kStats, bool kQueue, bool kEarly, int kPath, int kPPT>
+__global__ void __launch_bounds__(tc_threads<kPPT>(), kTcCtasPerSm) k_render_tc(TcParams p) {
     constexpr bool kSplit = kPath == kPathSplit;
     constexpr bool kCC = kPath == kPathCudaCore;
+    constexpr bool k2 = kPPT == 2;
+    constexpr int kCW = consumer_warps<kPPT>();
+    static_assert(kPPT == 1 || (kPPT == 2 && !kInspect), "two pixels a thread: rendering only");
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
@@ -307,15 +324,17 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     __shared__ unsigned long long s_acc[3];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const bool producer = warp == kConsumerWarps;
-    // consumer warp block (8 x 4 pixels) of a tile, and this thread's pixel in it; warps 0-3 cover
-    // rows 0-7 (MMA half 0, U rows 0-127), warps 4-7 rows 8-15 (half 1, U rows 128-255)
-    const int half = (warp >> 2) & 1;
-    const int bx = warp & 1, by = (warp >> 1) & 3;
-    const int lx = 8 * bx + (lane & 7), ly = 4 * by + (lane >> 3);
+    const bool producer = warp == kCW;
+    // consumer warp block of a tile, and this thread's pixel in it.  One pixel a thread: 8 x 4 blocks,
+    // warps 0-3 cover rows 0-7 (MMA half 0, U rows 0-127), warps 4-7 rows 8-15 (half 1, U rows
+    // 128-255).  Two: 8 x 8 blocks, warp w rows 8 (w >> 1) .. + 7; pixel (lx, ly) in half 0 (U row
+    // 32 w + lane) and (lx, ly + 4) in half 1 (U row 128 + 32 w + lane), both at TMEM lane 32 w + lane.
+    const int half = k2 ? 0 : (warp >> 2) & 1;
+    const int bx = warp & 1, by = k2 ? (warp >> 1) & 1 : (warp >> 1) & 3;
+    const int lx = 8 * bx + (lane & 7), ly = (k2 ? 8 : 4) * by + (lane >> 3);
     // this warp's pixel-centre rectangle, tile-local
     const float bx0 = 8.f * bx - 7.5f, bx1 = bx0 + 7.f;
-    const float by0 = 4.f * by - 7.5f, by1 = by0 + 3.f;
+    const float by0 = (k2 ? 8.f : 4.f) * by - 7.5f, by1 = by0 + (k2 ? 7.f : 3.f);
     uint8_t* sA = smem + kSmemA;
     const uint32_t mbar0 = smem_u32(&s_mbar[0]);
     const int enc = kSplit ? (int)kEncF16Split : p.enc;
@@ -323,6 +342,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
     // CUDA-core product: this thread's tile-local pixel vector (u1..u5; u0 = 1) in registers
     const float ux = (float)lx + 0.5f - kTile / 2, uy = (float)ly + 0.5f - kTile / 2;
     const float uxx = ux * ux, uxy = ux * uy, uyy = uy * uy;
+    const float uyB = uy + 4.f;   // the second pixel (two a thread)
+    const float uxyB = ux * uyB, uyyB = uyB * uyB;
 
     if (producer) {
         if (!kCC) {
@@ -352,6 +373,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
         uint32_t w[8];
         encode_row<false>(enc, u, w);
         store_row(sA, t, w);
+        if (k2) {   // U row 128 + t: the thread's second pixel, four rows below
+            const float dyB = dy + 4.f;
+            const float uB[6] = {1.f, dx, dyB, dx * dx, dx * dyB, dyB * dyB};
+            encode_row<false>(enc, uB, w);
+            store_row(sA, 128 + t, w);
+        }
     }
     fence_async_smem();
     tc_fence_before();
@@ -395,6 +422,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
         const int tx = tile % vd.cam.grid_w, ty = tile / vd.cam.grid_w;
         const int px_i = tx * kTile + lx, py_i = ty * kTile + ly;
         const bool inside = !producer && tile_ok && px_i < vd.cam.width && py_i < vd.cam.height;
+        const bool insideB = k2 && !producer && tile_ok && px_i < vd.cam.width && py_i + 4 < vd.cam.height;
         const float cx = (float)(tx * kTile + kTile / 2), cy = (float)(ty * kTile + kTile / 2);   // p(T)
         const uint32_t start = vd.ranges[2 * tile], end = vd.ranges[2 * tile + 1];
         uint32_t stop = tile_ok ? end : start;
@@ -535,8 +563,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
 
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
         uint32_t last = 0, n_eval = end - start, n_blend = 0, cols = 0, walked = 0;
-        bool done = !inside;
-        float thr = done ? kInf : kBeta2Cull;
+        // the second pixel (two a thread)
+        float TB = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+        uint32_t lastB = 0, n_evalB = end - start, n_blendB = 0;
+        float thrB = insideB ? kBeta2Cull : kInf;
+        bool done = !inside && !insideB;
+        float thr = (k2 ? !inside : done) ? kInf : kBeta2Cull;
         uint32_t mask_cur = 0;
 
         // prologue: batches 0 and 1 staged, MMA 0 complete, MMA 1 issued, masks of batch 0 known
@@ -595,11 +627,18 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 while (m) {
                     const int j = __clz(__brev(m));   // lowest marked column
                     m &= m - 1;
-                    float b2;
+                    float b2, b2B = 0.f;
                     if (kCC) {   // u^T v on CUDA cores, FP32 (broadcast shared-memory reads)
                         const float4* sV = reinterpret_cast<const float4*>(smem + kSmemVf + (k % 3u) * (kN * 32));
                         const float4 va = sV[2 * j], vb = sV[2 * j + 1];
                         b2 = fmaf(vb.y, uyy, fmaf(vb.x, uxy, fmaf(va.w, uxx, fmaf(va.z, uy, fmaf(va.y, ux, va.x)))));
+                        if (k2)
+                            b2B = fmaf(vb.y, uyyB, fmaf(vb.x, uxyB, fmaf(va.w, uxx, fmaf(va.z, uyB, fmaf(va.y, ux, va.x)))));
+                    } else if (k2) {   // both halves' accumulators, one wait
+                        uint32_t r = tmem_ld1(taddr + (uint32_t)j), rB = tmem_ld1(taddr + (uint32_t)(kN + j));
+                        tmem_wait_ld2(r, rB);
+                        b2 = __uint_as_float(r);
+                        b2B = __uint_as_float(rB);
                     } else {
                         uint32_t r = tmem_ld1(taddr + (uint32_t)j);
                         tmem_wait_ld1(r);
@@ -628,8 +667,29 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                         n_blend += blend ? 1u : 0u;
                     }
                     thr = term ? kInf : thr;
+                    if (k2) {   // the second pixel: the same steps
+                        const float eB = ex2_approx(b2B);
+                        const bool passB = kEarly ? b2B >= thrB : (eB >= kCullAlpha && thrB < kInf);
+                        const float aB = fminf(p.alpha_max, eB);
+                        const float TnB = fmaf(-aB, TB, TB);
+                        const bool termB = passB && (TnB < kTmin);
+                        const bool blendB = passB && !termB;
+                        const float TbB = blendB ? TnB : TB;
+                        const float wB = TB - TbB;
+                        D0 = fmaf(c.x, wB, D0);
+                        D1 = fmaf(c.y, wB, D1);
+                        D2 = fmaf(c.z, wB, D2);
+                        TB = TbB;
+                        lastB = blendB ? pos : lastB;
+                        if (kStats) {
+                            n_evalB = termB ? pos : n_evalB;
+                            n_blendB += blendB ? 1u : 0u;
+                        }
+                        thrB = termB ? kInf : thrB;
+                    }
                 }
-                done = thr == kInf;   // terminated (thr starts infinite for pixels outside the image)
+                // terminated (thr starts infinite for pixels outside the image)
+                done = k2 ? thr == kInf && thrB == kInf : thr == kInf;
                 // marks of batch k + 1 (staged in the previous window, so stable during this one) before
                 // the barrier: warps that finish early take this cost while the slowest one walks
                 if (k + 1 < nbat)
@@ -659,12 +719,25 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_render_tc(TcParams
                 vd.T_final[pix] = T;
                 vd.n_contrib[pix] = last;
             }
+            if (insideB) {
+                size_t pix = (size_t)(py_i + 4) * vd.cam.width + px_i;
+                size_t plane = (size_t)vd.cam.width * vd.cam.height;
+                vd.img[pix] = D0 + TB * p.bg[0];
+                vd.img[plane + pix] = D1 + TB * p.bg[1];
+                vd.img[2 * plane + pix] = D2 + TB * p.bg[2];
+                vd.T_final[pix] = TB;
+                vd.n_contrib[pix] = lastB;
+            }
             if (kStats) {
                 if (inside) {
                     atomicAdd(&s_acc[0], (unsigned long long)n_blend);
                     atomicAdd(&s_acc[1], (unsigned long long)(n_eval - n_blend));
                 }
-                if (lane == 0 && !producer) atomicAdd(&s_acc[2], (unsigned long long)cols * 32ull);
+                if (insideB) {
+                    atomicAdd(&s_acc[0], (unsigned long long)n_blendB);
+                    atomicAdd(&s_acc[1], (unsigned long long)(n_evalB - n_blendB));
+                }
+                if (lane == 0 && !producer) atomicAdd(&s_acc[2], (unsigned long long)cols * (32ull * kPPT));
             }
         } else if (!producer) {
             const int pix = ly * kTile + lx;
@@ -727,26 +800,25 @@ bool device_is_sm103(int* sms = nullptr) {
     return true;
 }
 
-// Whether the dynamic shared memory size has been raised for an instance on a device (one bit per
-// instance; function attributes are per device).
+// Whether the dynamic shared memory size has been raised for an instance on a device (a flag per
+// instance and device; function attributes are per device).
 std::mutex g_attr_mutex;
-uint64_t g_attr_set[kMaxDevices] = {};
 
-template <bool kInspect, bool kStats, bool kQueue, bool kEarly, int kPath>
+template <bool kInspect, bool kStats, bool kQueue, bool kEarly, int kPath, int kPPT>
 tcgs_status launch_tc_t(const TcParams& p, int blocks, cudaStream_t s) {
-    auto kern = k_render_tc<kInspect, kStats, kQueue, kEarly, kPath>;
+    static bool attr_set[kMaxDevices] = {};
+    auto kern = k_render_tc<kInspect, kStats, kQueue, kEarly, kPath, kPPT>;
     DeviceInfo d;
     if (!current_device_info(&d)) return TCGS_ERR_CUDA;
-    const uint64_t bit = 1ull << (32 * kInspect + 16 * kStats + 8 * kQueue + 4 * kEarly + kPath);
     {
         std::lock_guard<std::mutex> lock(g_attr_mutex);
-        if (!(g_attr_set[d.device] & bit)) {
+        if (!attr_set[d.device]) {
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
                 return TCGS_ERR_CUDA;
-            g_attr_set[d.device] |= bit;
+            attr_set[d.device] = true;
         }
     }
-    launch_pdl(kern, blocks, kTcThreads, kSmemDyn, s, p);
+    launch_pdl(kern, blocks, tc_threads<kPPT>(), kSmemDyn, s, p);
     count_launches(1);
     TCGS_CHECK_LAUNCH();
     return TCGS_OK;
@@ -759,15 +831,20 @@ tcgs_status launch_tc_t(const TcParams& p, int blocks, cudaStream_t s) {
 template <bool kInspect, bool kStats, bool kQueue>
 tcgs_status launch_tc(const TcParams& p, int blocks, cudaStream_t s) {
     if constexpr (kInspect) {
-        return launch_tc_t<kInspect, kStats, kQueue, true, kPathGeneric>(p, blocks, s);
+        return launch_tc_t<kInspect, kStats, kQueue, true, kPathGeneric, 1>(p, blocks, s);
     } else {
-        if (p.cuda_core)
-            return p.early_cull ? launch_tc_t<kInspect, kStats, kQueue, true, kPathCudaCore>(p, blocks, s)
-                                : launch_tc_t<kInspect, kStats, kQueue, false, kPathCudaCore>(p, blocks, s);
+        const bool two = p.ppt == 2 && p.early_cull;
+        if (p.cuda_core) {
+            if (two) return launch_tc_t<kInspect, kStats, kQueue, true, kPathCudaCore, 2>(p, blocks, s);
+            return p.early_cull ? launch_tc_t<kInspect, kStats, kQueue, true, kPathCudaCore, 1>(p, blocks, s)
+                                : launch_tc_t<kInspect, kStats, kQueue, false, kPathCudaCore, 1>(p, blocks, s);
+        }
         const bool split = p.enc == kEncF16Split && !p.global;
-        if (!p.early_cull) return launch_tc_t<kInspect, kStats, kQueue, false, kPathGeneric>(p, blocks, s);
-        if (split) return launch_tc_t<kInspect, kStats, kQueue, true, kPathSplit>(p, blocks, s);
-        return launch_tc_t<kInspect, kStats, kQueue, true, kPathGeneric>(p, blocks, s);
+        if (!p.early_cull) return launch_tc_t<kInspect, kStats, kQueue, false, kPathGeneric, 1>(p, blocks, s);
+        if (split)
+            return two ? launch_tc_t<kInspect, kStats, kQueue, true, kPathSplit, 2>(p, blocks, s)
+                       : launch_tc_t<kInspect, kStats, kQueue, true, kPathSplit, 1>(p, blocks, s);
+        return launch_tc_t<kInspect, kStats, kQueue, true, kPathGeneric, 1>(p, blocks, s);
     }
 }
 
@@ -829,6 +906,8 @@ tcgs_status launch_render_tc(const tcgs_camera* cam, const tcgs_render_opts* opt
     p.status = opts->device_status;
     p.tile_cull = p.global ? 0 : opts->tile_cull;   // the ablation walks every entry
     p.early_cull = opts->early_cull;
+    if (opts->pixels_per_thread < 0 || opts->pixels_per_thread > 2) return TCGS_ERR_INVALID;
+    p.ppt = opts->pixels_per_thread == 2 ? 2 : 1;
     const int tiles = p.v[0].cam.grid_w * p.v[0].cam.grid_h;
     if (opts->tile_order && !opts->work_counter) return TCGS_ERR_INVALID;
     if (opts->tile_order && !p.global && tiles > sms * kTcCtasPerSm) {

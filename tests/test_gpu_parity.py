@@ -479,6 +479,49 @@ def test_persistent_render_matches_one_cta_per_tile(tc, name, make):
     assert (np.diff(order)[same] > 0).all()   # tile order inside a group
 
 
+@pytest.mark.parametrize("name,make", [
+    ("diff_crop_320x180", lambda: scenes.differentiation(P=20_000, width=320, height=180, seed=13)[:2]),
+    ("plain_ragged_200x134", lambda: scenes.plain_forward(P=1500, width=200, height=134, seed=11)),
+    ("large_crop_960x540", lambda: scenes.large(P=20_000, width=960, height=540, seed=14))])
+def test_two_pixels_a_thread_render_the_same_image(tc, name, make):
+    """The renderer instance with two pixels a consumer thread (8 x 8 warp blocks, one pixel in each
+    MMA half) gives the image, T and n_contrib of the one-pixel instance bit for bit, with the tensor-
+    core and the CUDA-core product, one CTA per tile and persistent, and the same blended and evaluated
+    fragment counts (only the executed slots differ: coarser block marks).  The ragged view's last
+    tile row is 6 pixels high, so some threads have only their first pixel inside the image."""
+    cam, sc = make()
+    dsc = {k: to_torch(v, DEV) if isinstance(v, np.ndarray) else v for k, v in sc.items()}
+    P = len(sc["opacity"])
+    cap = int(oracle.project(cam, scene64(sc))["tiles_touched"].sum()) + 64
+    r = tc.Renderer(cam, P, cap, device=DEV, stats=True, persistent=False, pixels_per_thread=1)
+    r.project(dsc)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    order = tc.tcgs_tile_order(r.cam, r.bins["tile_ranges"])
+    counter = torch.zeros(1, dtype=torch.int32, device=DEV)
+    for prec in ("tc_fp16_split", "fp32_frag2mat"):
+        res = {}
+        for ppt in (1, 2):
+            for persistent in (False, True):
+                r.stats.zero_()
+                opts = tc.render_opts(prec, tile_stats=r.stats, pixels_per_thread=ppt,
+                                      tile_order=order if persistent else None,
+                                      work_counter=counter if persistent else None)
+                o = tc.tcgs_render_fwd(r.cam, opts, r.bins["tile_ranges"], r.bins["ids_sorted"], r.proj["mean2d"],
+                                       r.proj["conic"], dsc["opacity"], r.proj["rgb"])
+                torch.cuda.synchronize()
+                res[(ppt, persistent)] = ({k: v.clone() for k, v in o.items()}, r.stats.clone())
+        base_img, base_st = res[(1, False)]
+        assert base_img["n_contrib"].max() > 0
+        for key, (img, st) in res.items():
+            for k in ("img", "T_final", "n_contrib"):
+                assert torch.equal(img[k], base_img[k]), (name, prec, key, k)
+            assert torch.equal(st[:, :2], base_st[:, :2]), (name, prec, key)   # blended, evaluated
+            assert torch.equal(st[:, 3], base_st[:, 3]), (name, prec, key)     # list lengths
+    assert tc.Renderer(cam, P, 16 * P, device=DEV).pixels_per_thread == 2
+    assert tc.Renderer(cam, P, 16 * P - 1, device=DEV).pixels_per_thread == 1
+
+
 @pytest.mark.parametrize("width,height", [(40, 24), (1920, 1080), (4160, 2176)])
 def test_tile_order_is_the_stable_longest_first_sort(tc, width, height):
     """tcgs_tile_order on synthetic list lengths spanning every length group (empty lists up to
