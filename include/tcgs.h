@@ -118,8 +118,9 @@ typedef struct {
                                 blocks, so every walked list entry serves 64 pixels at the cost of coarser
                                 block marks: faster for views of large footprints, whose batches mark most
                                 entries anyway, slower for views of small ones.  Honoured by
-                                TCGS_TC_FP16_SPLIT and TCGS_FP32_FRAG2MAT with early_cull = 1; the other
-                                configurations render with one.  The image is the same either way */
+                                TCGS_TC_FP16_SPLIT and TCGS_FP32_FRAG2MAT with early_cull = 1 in
+                                tcgs_render_fwd; the other configurations, and tcgs_render_fwd_batched,
+                                render with one.  The image is the same either way */
 } tcgs_render_opts;
 
 /* Human-readable name of a status code (static string). */
