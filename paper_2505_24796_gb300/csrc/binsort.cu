@@ -9,6 +9,11 @@
 //   5. tile ranges from adjacent tile-id changes.
 // Because every pass is stable and duplication preserves the depth order, the result is the
 // (tile, depth, id) order of the 64-bit-key sort, while only 1-2 passes touch the N splats.
+// With two tile passes whose high tile bits and Gaussian id fit one 32-bit word together, the first
+// pass writes that word alone, the second sorts the words and writes the ids, and the ranges come
+// from per-tile counts taken in the second pass's histogram (the low tile byte of a position is its
+// digit run in the first pass's output): from the duplication to the ranges 36 instead of 52 bytes
+// per splat, and no ranges pass.
 //
 // Radix sort design (per pass): a fixed grid of G blocks; block b owns one contiguous key
 // range.  hist: per-block 256-bin digit counts (+ global digit totals).  scan: one block per
@@ -78,34 +83,88 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* warp_sums, T& total) {
 
 // ---------------------------------------------------------------- radix sort passes
 
-template <int KI>
+// Lower digits a tile-counting histogram block keeps in shared memory (the digit of its first key
+// and the next kTileWin - 1); the keys of any later digit are counted in global memory directly.
+constexpr int kTileWin = 4;
+
+// Per-block digit counts of one pass over a contiguous key range (+ global digit totals).
+// kTileCount (second pass of the packed tile sort): the keys are packed words (tile >> 8, id), whose
+// low tile byte is the position's digit in the first pass's output (runs of lo_total[d] keys, in
+// digit order), so the block also counts its splats per tile, adding them to tile_counts[2 t + 1].
+template <int KI, bool kTileCount = false>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
                                                          const uint32_t* n_dev, int shift, uint32_t mask, int G,
                                                          uint32_t* __restrict__ hist,
-                                                         uint32_t* __restrict__ digit_total) {
+                                                         uint32_t* __restrict__ digit_total,
+                                                         const uint32_t* __restrict__ lo_total,
+                                                         uint32_t* __restrict__ tile_counts) {
     pdl_trigger();
     pdl_wait();
     __shared__ uint32_t h[kWarps][kRadix];
+    __shared__ uint32_t s_start[kTileCount ? kRadix + 1 : 1];   // first position of each low digit's run
+    __shared__ uint32_t s_ws[kWarps];
+    __shared__ uint32_t lc[kTileCount ? kTileWin * kRadix : 1];  // window of low digits x high digits
     const int t = threadIdx.x, warp = t >> 5;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) h[w][t] = 0;
-    __syncthreads();
     uint32_t lo, hi;
     block_range<kThreads * KI>(load_n(n_host, n_dev), G, lo, hi);
-    for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+    if constexpr (kTileCount) {
+        uint32_t n_lo;
+        s_start[t] = block_exclusive_scan<uint32_t, kThreads>(lo_total[t], s_ws, n_lo);   // barriers inside
+        if (t == 0) s_start[kRadix] = n_lo;
+#pragma unroll
+        for (int w = 0; w < kTileWin; ++w) lc[w * kRadix + t] = 0;
+    }
+    __syncthreads();
+    // the largest d with s_start[d] <= i is the (non-empty) low digit whose run holds position i
+    auto digit_at = [&](uint32_t i) {
+        int a = 0, b = kRadix - 1;
+        while (a < b) {
+            const int m = (a + b + 1) >> 1;
+            if (s_start[m] <= i) a = m; else b = m - 1;
+        }
+        return (uint32_t)a;
+    };
+    uint32_t d0 = 0;   // the window's first low digit
+    if constexpr (kTileCount) {
+        d0 = lo < hi ? digit_at(lo) : 0u;
+        uint32_t d = lo + t < hi ? digit_at(lo + t) : 0u;
+        for (uint32_t i = lo + t; i < hi; i += kThreads) {
+            while (s_start[d + 1] <= i) ++d;   // s_start[256] = n > i ends the walk by digit 255
+            const uint32_t hd = (keys[i] >> shift) & mask;
+            atomicAdd(&h[warp][hd], 1u);
+            const uint32_t w = d - d0;
+            if (w < (uint32_t)kTileWin) atomicAdd(&lc[w * kRadix + hd], 1u);
+            else atomicAdd(&tile_counts[2 * ((hd << 8) | d) + 1], 1u);
+        }
+    } else {
+        for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+    }
     __syncthreads();
     uint32_t s = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) s += h[w][t];
     hist[(size_t)t * G + blockIdx.x] = s;
     if (s) atomicAdd(&digit_total[t], s);
+    if constexpr (kTileCount) {
+        for (int b = t; b < kTileWin * kRadix; b += kThreads) {
+            const uint32_t c = lc[b];   // nonzero only for tiles that hold splats
+            if (c) atomicAdd(&tile_counts[2 * (((uint32_t)(b & (kRadix - 1)) << 8) | (d0 + (uint32_t)(b >> 8))) + 1], c);
+        }
+    }
 }
 
 // Block d turns row d of hist (the G per-block counts of digit d) into global offsets:
 // offset(d, b) = sum_{d' < d} total(d') + sum_{b' < b} count(d, b').
+// kTileRanges (second pass of the packed tile sort): digit d is the high byte of the tile id, so
+// tiles 256 d .. 256 d + 255 lie in that order from the digit's offset on; block d turns their counts
+// (tile_counts[2 t + 1], from the histogram) into [start, end) ranges, [0, 0) for an empty tile.
+template <bool kTileRanges = false>
 __global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ hist,
                                                          const uint32_t* __restrict__ digit_total,
-                                                         uint32_t* __restrict__ digit_total_next, int G) {
+                                                         uint32_t* __restrict__ digit_total_next, int G,
+                                                         uint32_t* __restrict__ tile_ranges, int num_tiles) {
     pdl_trigger();
     pdl_wait();
     __shared__ uint32_t ws[kWarps];
@@ -125,20 +184,39 @@ __global__ void __launch_bounds__(kThreads) k_radix_scan(uint32_t* __restrict__ 
         run += chunk;
     }
     if (d == 0) digit_total_next[t] = 0u;
+    if constexpr (kTileRanges) {
+        if (d * kRadix < num_tiles) {   // uniform over the block
+            const uint32_t tile = (uint32_t)(d * kRadix + t);
+            const uint32_t c = tile < (uint32_t)num_tiles ? tile_ranges[2 * tile + 1] : 0u;
+            uint32_t sum;
+            const uint32_t start = tot + block_exclusive_scan<uint32_t, kThreads>(c, ws, sum);
+            if (tile < (uint32_t)num_tiles) {
+                tile_ranges[2 * tile] = c ? start : 0u;
+                tile_ranges[2 * tile + 1] = c ? start + c : 0u;
+            }
+        }
+    }
 }
+
+// Output forms of a scatter pass: key-value pairs; the packed tile sort's first pass (keys are
+// tile ids, values Gaussian ids; it writes one word, (tile >> 8) << pack_shift | id, to vals_out); its
+// second pass (keys are those words, there are no values; it writes the ids, the low pack_shift bits,
+// to vals_out).
+enum : int { kScatterPairs = 0, kScatterPackOut = 1, kScatterPackedIn = 2 };
 
 // Stable scatter of one 8-bit digit.  Per tile of kThreads x KI keys: warp-level ranks
 // (__match_any_sync), a per-digit prefix over the warps, keys and values regrouped by digit in
 // shared memory, then written out so that consecutive threads write consecutive addresses of each
 // digit's run (coalesced).  Keys of the next tile are loaded one tile ahead; a tile's values are
 // requested before its keys are ranked.
-template <int KI>
+template <int KI, int kMode = kScatterPairs>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, uint32_t n_host,
                                                             const uint32_t* n_dev, int shift, uint32_t mask, int G,
-                                                            const uint32_t* __restrict__ offsets) {
+                                                            const uint32_t* __restrict__ offsets, int pack_shift) {
+    constexpr bool kVals = kMode != kScatterPackedIn;
     pdl_trigger();
     pdl_wait();
     constexpr int TI = kThreads * KI;
@@ -146,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     __shared__ uint32_t boff[kRadix];     // next global position of each digit for this block
     __shared__ uint32_t tstart[kRadix];   // tile-local start of each digit's run
     __shared__ uint32_t ws[kWarps];
-    __shared__ uint32_t sk[TI], sv[TI];
+    __shared__ uint32_t sk[TI], sv[kVals ? TI : 1];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     uint32_t lo, hi;
     block_range<TI>(load_n(n_host, n_dev), G, lo, hi);
@@ -172,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
 #pragma unroll
         for (int r = 0; r < KI; ++r) {
             const uint32_t i = base + r * 32 + lane;
-            v[r] = i < hi ? vals_in[i] : 0u;
+            v[r] = kVals && i < hi ? vals_in[i] : 0u;
         }
         if (tile + TI < hi) load_keys(tile + TI);
 #pragma unroll
@@ -214,9 +292,11 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
                 pos[r] = 0xFFFFFFFFu;
             }
         }
+        if constexpr (kVals) {
 #pragma unroll
-        for (int r = 0; r < KI; ++r) {
-            if (pos[r] != 0xFFFFFFFFu) sv[pos[r]] = v[r];
+            for (int r = 0; r < KI; ++r) {
+                if (pos[r] != 0xFFFFFFFFu) sv[pos[r]] = v[r];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -226,8 +306,14 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
                 const uint32_t key = sk[i];
                 const uint32_t d = (key >> shift) & mask;
                 const uint32_t gp = boff[d] + (i - tstart[d]);
-                keys_out[gp] = key;
-                vals_out[gp] = sv[i];
+                if constexpr (kMode == kScatterPairs) {
+                    keys_out[gp] = key;
+                    vals_out[gp] = sv[i];
+                } else if constexpr (kMode == kScatterPackOut) {
+                    vals_out[gp] = ((key >> 8) << pack_shift) | sv[i];
+                } else {
+                    vals_out[gp] = key & ((1u << pack_shift) - 1u);
+                }
             }
         }
         __syncthreads();
@@ -477,6 +563,10 @@ __device__ int2 row_span(const Cover& v, const Reach& e, int ty, int x0, int x1)
 constexpr int kRowMinWidth = 6;
 // The row path runs when the caller's splat capacity allows at least this many splats per Gaussian.
 constexpr int kRowsCapacityPerGaussian = 32;
+// The packed tile sort runs for capacities of at least this many splats: its per-tile counting costs
+// more than the traffic it saves on short lists (bin_sort of the 2.3M-splat 1080p frame 0.226 ->
+// 0.228 ms; 11.6M splats 0.527 -> 0.510 ms; 605M splats 15.8 -> 14.2 ms).
+constexpr int64_t kPackedTileSortCapacity = (int64_t)1 << 23;
 // The binning kernels keep 8 blocks of 256 threads resident per SM (at most 32 registers a thread):
 // their tile path is bound by instruction latency and needs all 8; the row path, out of line, is
 // held to the same registers.
@@ -1040,19 +1130,24 @@ inline int sort_blocks(int64_t n) {
 }
 
 // One LSD pass on the digit of `bits` (<= 8) bits at `shift`; digit totals ping-pong between two
-// 256-word buffers (the scan of a pass zeroes the buffer the next pass accumulates into).
-template <int KI>
+// 256-word buffers (the scan of a pass zeroes the buffer the next pass accumulates into, after this
+// pass's histogram has read it: the previous pass's totals).  kMode and kTiles select the passes of
+// the packed tile sort (k_radix_scatter, k_radix_hist, k_radix_scan).
+template <int KI, int kMode = kScatterPairs, bool kTiles = false>
 inline void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n_host,
                        const uint32_t* n_dev, int shift, int bits, int G, const Workspace& w, int pass,
-                       cudaStream_t s) {
+                       cudaStream_t s, int pack_shift = 0, uint32_t* tile_ranges = nullptr, int num_tiles = 0) {
     uint32_t* tot = w.digit_total + (pass & 1) * kRadix;
     uint32_t* nxt = w.digit_total + ((pass + 1) & 1) * kRadix;
     const uint32_t mask = (1u << bits) - 1u;
-    launch_pdl(k_radix_hist<KI>, G, kThreads, 0, s, kin, n_host, n_dev, shift, mask, G, w.hist, tot);
+    launch_pdl(k_radix_hist<KI, kTiles>, G, kThreads, 0, s, kin, n_host, n_dev, shift, mask, G, w.hist, tot,
+               (const uint32_t*)nxt, tile_ranges);
     count_launches(1);
-    launch_pdl(k_radix_scan, kRadix, kThreads, 0, s, w.hist, tot, nxt, G);
+    launch_pdl(k_radix_scan<kTiles>, kRadix, kThreads, 0, s, w.hist, (const uint32_t*)tot, nxt, G, tile_ranges,
+               num_tiles);
     count_launches(1);
-    launch_pdl(k_radix_scatter<KI>, G, kThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift, mask, G, w.hist);
+    launch_pdl(k_radix_scatter<KI, kMode>, G, kThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift, mask, G,
+               (const uint32_t*)w.hist, pack_shift);
     count_launches(1);
 }
 
@@ -1163,9 +1258,17 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     int tile_bits = 0;
     while ((1 << tile_bits) < num_tiles) ++tile_bits;
     int tpasses = tile_bits <= 8 ? 1 : (tile_bits <= 16 ? 2 : 3);
+    // Two tile passes with the high tile bits and the Gaussian id in one word: the first pass writes
+    // (tile >> 8, id) packed, the second sorts those words alone, writes the ids and, from per-tile
+    // counts, the ranges (a third of the splat traffic and the ranges pass saved), for capacities of
+    // at least kPackedTileSortCapacity splats (the same lists either way).
+    int id_bits = 1;
+    while (id_bits < 31 && ((int64_t)1 << id_bits) < (int64_t)P) ++id_bits;   // ids 0 .. P - 1
+    const bool packed = tpasses == 2 && (tile_bits - 8) + id_bits <= 32 && splat_capacity >= kPackedTileSortCapacity;
     uint32_t* kbuf[2] = {w.sk_a, w.sk_b};
     uint32_t* vbuf[2] = {ids_sorted, w.sv_b};
-    int src = (tpasses & 1) ? 1 : 0;
+    int src = packed ? 0 : ((tpasses & 1) ? 1 : 0);
+    if (packed) vbuf[0] = w.sv_b;   // the duplication writes (sk_a, sv_b)
     const int dup_blocks = (P + kThreads - 1) / kThreads;
     if (rows)
         launch_pdl(k_duplicate<true, true>, dup_blocks, kThreads, 0, s, dc, (uint32_t)P, order, w.offsets, w.counts,
@@ -1180,6 +1283,17 @@ tcgs_status bin_sort(const tcgs_camera* cam, int32_t P, const float* mean2d, con
     TCGS_CHECK_LAUNCH();
     // 4. stable sort by tile id, 8 bits per pass (an even split of the tile bits measured slower)
     int Gs = sort_blocks<kItemsSplat>(splat_capacity);
+    if (packed) {
+        radix_pass<kItemsSplat, kScatterPackOut>(w.sk_a, w.sv_b, nullptr, w.sk_b, 0u, w.n_u32, 0, 8, Gs, w, pass, s,
+                                                 id_bits);
+        ++pass;
+        // 5. ranges from the second pass's per-tile counts (the tile ranges were zeroed by k_bin_keys)
+        radix_pass<kItemsSplat, kScatterPackedIn, true>(w.sk_b, nullptr, nullptr, ids_sorted, 0u, w.n_u32, id_bits,
+                                                        tile_bits - 8, Gs, w, pass, s, id_bits, tile_ranges,
+                                                        num_tiles);
+        TCGS_CHECK_LAUNCH();
+        return TCGS_OK;
+    }
     for (int tp = 0, shift = 0; tp < tpasses; ++tp, ++pass) {
         const int bits = tile_bits - shift < 8 ? tile_bits - shift : 8;
         radix_pass<kItemsSplat>(kbuf[src], vbuf[src], kbuf[src ^ 1], vbuf[src ^ 1], 0u, w.n_u32, shift, bits, Gs, w,

@@ -182,6 +182,44 @@ def test_bin_sort_small_view_path_matches_multi_block_path(tc, name, make, exact
         np.testing.assert_array_equal(res[0][2], b["ranges"])
 
 
+# the capacity from which two tile passes run on packed (tile >> 8, id) words (binsort.cu)
+PACKED_TILE_SORT_CAPACITY = 1 << 23
+
+
+@pytest.mark.parametrize("exact", [False, True])
+@pytest.mark.parametrize("name,make", [
+    ("large_crop_960x540", lambda: scenes.large(P=20_000, width=960, height=540, seed=14)),
+    ("precision_crop_1024x512", lambda: scenes.precision(P=100_000, width=1024, height=512, seed=13))])
+def test_packed_tile_sort_matches_key_value_passes(tc, name, make, exact):
+    """Views of more than 256 tiles sort their splats in two tile passes: as key-value pairs followed by
+    a ranges pass below a capacity of 2^23 splats, and from 2^23 on as packed (tile >> 8, id) words
+    whose second pass takes the ranges from per-tile counts.  Both give the same N, lists and ranges
+    (empty tiles [0, 0)); with the rectangle coverage both equal the oracle's lists."""
+    cam, sc = make()
+    pr = oracle.project(cam, scene64(sc))
+    inp = dict(mean2d=f32(pr["mean2d"]), radius=pr["radius"], depth=f32(pr["depth"]), conic=f32(pr["conic"]))
+    b = oracle.bin_sort(cam, inp["mean2d"], inp["radius"], inp["depth"])
+    gw, gh = oracle.grid(cam)
+    assert gw * gh > 256 and b["n"] + 17 < PACKED_TILE_SORT_CAPACITY
+    m = to_torch(inp["mean2d"], DEV); r = to_torch(inp["radius"].astype(np.int32), DEV)
+    d = to_torch(inp["depth"], DEV)
+    kw = dict(conic=to_torch(inp["conic"], DEV), opacity=to_torch(sc["opacity"], DEV)) if exact else {}
+    res = []
+    for cap in (b["n"] + 17, PACKED_TILE_SORT_CAPACITY):
+        out = tc.tcgs_bin_sort(cam, m, r, d, capacity=cap, **kw)
+        torch.cuda.synchronize()
+        assert int(out["status"].item()) == 0
+        n = int(out["n_splats"].item())
+        res.append((n, out["ids_sorted"].cpu().numpy()[:n], out["tile_ranges"].cpu().numpy()))
+    assert res[1][0] == res[0][0]
+    np.testing.assert_array_equal(res[1][1], res[0][1])
+    np.testing.assert_array_equal(res[1][2], res[0][2])
+    if not exact:
+        assert res[1][0] == b["n"]
+        np.testing.assert_array_equal(res[1][1], b["ids"])
+        np.testing.assert_array_equal(res[1][2], b["ranges"])
+
+
 def test_bin_sort_capacity_overflow_reports_status(tc):
     cam, sc = scenes.plain_forward()
     pr = oracle.project(cam, scene64(sc))
