@@ -83,14 +83,11 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* warp_sums, T& total) {
 
 // ---------------------------------------------------------------- radix sort passes
 
-// Lower digits a tile-counting histogram block keeps in shared memory (the digit of its first key
-// and the next kTileWin - 1); the keys of any later digit are counted in global memory directly.
-constexpr int kTileWin = 4;
-
 // Per-block digit counts of one pass over a contiguous key range (+ global digit totals).
 // kTileCount (second pass of the packed tile sort): the keys are packed words (tile >> 8, id), whose
 // low tile byte is the position's digit in the first pass's output (runs of lo_total[d] keys, in
-// digit order), so the block also counts its splats per tile, adding them to tile_counts[2 t + 1].
+// digit order), so the block takes its range one such run at a time, and after each run adds its
+// per-digit counts to that run's tiles (tile_counts[2 t + 1]) before summing them into the block's.
 template <int KI, bool kTileCount = false>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
                                                          const uint32_t* n_dev, int shift, uint32_t mask, int G,
@@ -103,56 +100,47 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
     __shared__ uint32_t h[kWarps][kRadix];
     __shared__ uint32_t s_start[kTileCount ? kRadix + 1 : 1];   // first position of each low digit's run
     __shared__ uint32_t s_ws[kWarps];
-    __shared__ uint32_t lc[kTileCount ? kTileWin * kRadix : 1];  // window of low digits x high digits
     const int t = threadIdx.x, warp = t >> 5;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) h[w][t] = 0;
     uint32_t lo, hi;
     block_range<kThreads * KI>(load_n(n_host, n_dev), G, lo, hi);
+    uint32_t s = 0;
     if constexpr (kTileCount) {
         uint32_t n_lo;
-        s_start[t] = block_exclusive_scan<uint32_t, kThreads>(lo_total[t], s_ws, n_lo);   // barriers inside
+        s_start[t] = block_exclusive_scan<uint32_t, kThreads>(lo_total[t], s_ws, n_lo);   // ends in a barrier
         if (t == 0) s_start[kRadix] = n_lo;
+        __syncthreads();
+        for (uint32_t a = lo; a < hi;) {   // uniform over the block
+            // the run holding position a: the largest d with s_start[d] <= a (a non-empty run)
+            int d = 0, e = kRadix - 1;
+            while (d < e) {
+                const int m = (d + e + 1) >> 1;
+                if (s_start[m] <= a) d = m; else e = m - 1;
+            }
+            const uint32_t b = s_start[d + 1] < hi ? s_start[d + 1] : hi;
+            for (uint32_t i = a + t; i < b; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+            __syncthreads();
+            uint32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < kTileWin; ++w) lc[w * kRadix + t] = 0;
-    }
-    __syncthreads();
-    // the largest d with s_start[d] <= i is the (non-empty) low digit whose run holds position i
-    auto digit_at = [&](uint32_t i) {
-        int a = 0, b = kRadix - 1;
-        while (a < b) {
-            const int m = (a + b + 1) >> 1;
-            if (s_start[m] <= i) a = m; else b = m - 1;
-        }
-        return (uint32_t)a;
-    };
-    uint32_t d0 = 0;   // the window's first low digit
-    if constexpr (kTileCount) {
-        d0 = lo < hi ? digit_at(lo) : 0u;
-        uint32_t d = lo + t < hi ? digit_at(lo + t) : 0u;
-        for (uint32_t i = lo + t; i < hi; i += kThreads) {
-            while (s_start[d + 1] <= i) ++d;   // s_start[256] = n > i ends the walk by digit 255
-            const uint32_t hd = (keys[i] >> shift) & mask;
-            atomicAdd(&h[warp][hd], 1u);
-            const uint32_t w = d - d0;
-            if (w < (uint32_t)kTileWin) atomicAdd(&lc[w * kRadix + hd], 1u);
-            else atomicAdd(&tile_counts[2 * ((hd << 8) | d) + 1], 1u);
+            for (int w = 0; w < kWarps; ++w) {
+                c += h[w][t];
+                h[w][t] = 0;
+            }
+            if (c) atomicAdd(&tile_counts[2 * (((uint32_t)t << 8) | (uint32_t)d) + 1], c);   // tile (t, d)
+            s += c;
+            __syncthreads();
+            a = b;
         }
     } else {
+        __syncthreads();
         for (uint32_t i = lo + t; i < hi; i += kThreads) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    uint32_t s = 0;
+        __syncthreads();
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += h[w][t];
+        for (int w = 0; w < kWarps; ++w) s += h[w][t];
+    }
     hist[(size_t)t * G + blockIdx.x] = s;
     if (s) atomicAdd(&digit_total[t], s);
-    if constexpr (kTileCount) {
-        for (int b = t; b < kTileWin * kRadix; b += kThreads) {
-            const uint32_t c = lc[b];   // nonzero only for tiles that hold splats
-            if (c) atomicAdd(&tile_counts[2 * (((uint32_t)(b & (kRadix - 1)) << 8) | (d0 + (uint32_t)(b >> 8))) + 1], c);
-        }
-    }
 }
 
 // Block d turns row d of hist (the G per-block counts of digit d) into global offsets:
@@ -563,9 +551,9 @@ __device__ int2 row_span(const Cover& v, const Reach& e, int ty, int x0, int x1)
 constexpr int kRowMinWidth = 6;
 // The row path runs when the caller's splat capacity allows at least this many splats per Gaussian.
 constexpr int kRowsCapacityPerGaussian = 32;
-// The packed tile sort runs for capacities of at least this many splats: its per-tile counting costs
-// more than the traffic it saves on short lists (bin_sort of the 2.3M-splat 1080p frame 0.226 ->
-// 0.228 ms; 11.6M splats 0.527 -> 0.510 ms; 605M splats 15.8 -> 14.2 ms).
+// The packed tile sort runs for capacities of at least this many splats: on short lists it gains
+// nothing (bin_sort of the 2.3M-splat 1080p frame 0.226 ms either way; 11.6M splats 0.527 -> 0.491 ms;
+// 605M splats 15.8 -> 12.7 ms).
 constexpr int64_t kPackedTileSortCapacity = (int64_t)1 << 23;
 // The binning kernels keep 8 blocks of 256 threads resident per SM (at most 32 registers a thread):
 // their tile path is bound by instruction latency and needs all 8; the row path, out of line, is
