@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     constexpr int TI = kThreads * KI;
     __shared__ uint32_t wcnt[kWarps][kRadix];
     __shared__ uint32_t boff[kRadix];     // next global position of each digit for this block
-    __shared__ uint32_t tstart[kRadix];   // tile-local start of each digit's run
+    __shared__ uint32_t gdelta[kRadix];   // global position of a digit's run minus its tile-local start
     __shared__ uint32_t ws[kWarps];
     __shared__ uint32_t sk[TI], sv[kVals ? TI : 1];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -276,22 +276,27 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
             pos[r] = ((valid ? d : 0x100u) << 16) | (before + __popc(peers & lt_mask));
         }
         __syncthreads();
-        // digit t: exclusive prefix over warps, the tile's count, and the tile-local run start
+        // digit t: the tile's count, the tile-local start of its run, and each warp's start in it
+        // (thread t alone touches column t of wcnt until the barrier)
         uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) total += wcnt[w][t];
+        uint32_t tile_total;
+        const uint32_t ts = block_exclusive_scan<uint32_t, kThreads>(total, ws, tile_total);
+        gdelta[t] = boff[t] - ts;   // the write-out reads one word per key (wraps like the sum it stands for)
+        uint32_t run = ts;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
             const uint32_t c = wcnt[w][t];
-            wcnt[w][t] = total;
-            total += c;
+            wcnt[w][t] = run;
+            run += c;
         }
-        uint32_t tile_total;
-        tstart[t] = block_exclusive_scan<uint32_t, kThreads>(total, ws, tile_total);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < KI; ++r) {
             const uint32_t d = pos[r] >> 16;
             if (d < 0x100u) {
-                const uint32_t lp = tstart[d] + wcnt[warp][d] + (pos[r] & 0xFFFFu);
+                const uint32_t lp = wcnt[warp][d] + (pos[r] & 0xFFFFu);
                 sk[lp] = k[r];
                 pos[r] = lp;
             } else {
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
             if (i < tile_n) {
                 const uint32_t key = sk[i];
                 const uint32_t d = (key >> shift) & mask;
-                const uint32_t gp = boff[d] + (i - tstart[d]);
+                const uint32_t gp = gdelta[d] + i;
                 if constexpr (kMode == kScatterPairs) {
                     keys_out[gp] = key;
                     vals_out[gp] = sv[i];
