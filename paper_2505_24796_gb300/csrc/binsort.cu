@@ -18,7 +18,8 @@
 // Radix sort design (per pass): a fixed grid of G blocks; block b owns one contiguous key
 // range.  hist: per-block 256-bin digit counts (+ global digit totals).  scan: one block per
 // digit turns the counts into global output offsets.  scatter: each warp ranks its 32-key
-// rounds with one ballot per digit bit, warps and tiles are chained in order, so the pass is stable.
+// rounds (by __match_any_sync and by ballots, alternately), warps and tiles are chained in order, so
+// the pass is stable.
 // No block ever waits on another block.
 #include <cuda.h>
 
@@ -54,9 +55,10 @@ __device__ __forceinline__ void block_range(uint32_t n, int G, uint32_t& lo, uin
 
 // The lanes of the warp whose kBits-bit value v equals this lane's, among the valid lanes (an invalid
 // lane's mask is its own business: the callers give each invalid lane a distinct low value and use
-// nothing of it).  One ballot per bit and one for validity: on GB300 the radix scatter ranks 5-10%
-// faster this way than with __match_any_sync (bin_sort 0.2285 -> 0.2172 ms on the 1080p frame,
-// 12.70 -> 11.46 ms on the 605M-splat 4K frame).
+// nothing of it).  One ballot per bit and one for validity.  __match_any_sync alone saturates the
+// shared-memory/MIO pipe of the radix scatter, these ballots alone its issue slots; the scatter
+// alternates the two by round (bin_sort with match only / ballots only / alternating: 0.2285 / 0.2162
+// / 0.2152 ms on the 1080p frame, 12.70 / 11.24 / 10.59 ms on the 605M-splat 4K frame).
 template <int kBits>
 __device__ __forceinline__ uint32_t warp_peers(uint32_t v, bool valid) {
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -267,7 +269,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
         for (int r = 0; r < KI; ++r) {
             const bool valid = base + r * 32 + lane < hi;
             const uint32_t d = valid ? ((k[r] >> shift) & mask) : (0x100u | lane);
-            const uint32_t peers = warp_peers<8>(d, valid);
+            // even rounds on the match unit, odd ones by ballots: the two pipes share the ranking
+            const uint32_t peers = (r & 1) == 0 ? __match_any_sync(0xffffffffu, d) : warp_peers<8>(d, valid);
             uint32_t before = 0;
             if (valid) before = wcnt[warp][d];
             __syncwarp();
