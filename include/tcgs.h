@@ -189,7 +189,9 @@ TCGS_API size_t tcgs_bin_sort_workspace_size(int32_t P, int64_t splat_capacity, 
  * an LSD radix sort whose depth digits run before duplication (on P keys) and whose tile
  * digits run after it (on N keys).  A small view (at most 256 tiles, P <= 8192 and
  * splat_capacity <= 32768) runs the same passes in two single-CTA kernels (4 launches in all,
- * against about 20), with the same result.
+ * against about 20), with the same result.  With two tile passes and splat_capacity >= 2^23, the
+ * first tile pass packs (tile >> 8, Gaussian id) into one word when they fit 32 bits, and the second
+ * writes the ranges from per-tile counts: again the same result.  Empty tiles get [0, 0).
  * In:  mean2d [P,2], radius [P], depth [P] (> 0 where radius > 0).
  * Out: ids_sorted [splat_capacity] uint32 (first N entries valid), tile_ranges [num_tiles, 2]
  *      uint32 [start, end), n_splats: device int64 = N, status: device int32 (TCGS_OK, or
